@@ -1,0 +1,185 @@
+/*
+ * fehmm.h -- C ABI of the GB300 batched FE-HMM / FE^2 periodic-RVE engine.
+ *
+ * Method: Eidel, Fischer, Gote, "A Nonlinear Finite Element Heterogeneous Multiscale
+ * Method for the Homogenization of Hyperelastic Solids and a Novel Staggered Two-Scale
+ * Solution Algorithm" (arXiv:1908.08292).  At every macro quadrature point a periodic
+ * representative volume element (RVE) is solved by Newton's method; it returns the
+ * homogenised first Piola-Kirchhoff stress Pbar = <P> (Eq. Average-of-P-and-F) and the
+ * homogenised tangent Abar = dPbar/dFbar, which the macro problem assembles into its
+ * residual and tangent (Sec. 3.1-3.3).
+ *
+ * Conventions
+ *  - Every function returns an int status: FEHMM_OK (0), a negative FEHMM_ERR_* code on an
+ *    API error, or (fehmm_rve_solve only) a positive count of quadrature points whose RVE
+ *    did not converge.  No exception crosses this boundary.  fehmm_status_str() names codes.
+ *  - Tensors are row-major: a d x d tensor T_iJ is stored at [i*d + J]; a fourth-order
+ *    tangent A_iJkL at [(i*d + J)*d*d + (k*d + L)].  Floating point data are FP64.
+ *  - "device" pointers are CUDA device (or managed) memory owned by the CALLER; "host"
+ *    pointers are ordinary host memory.  The library copies what it needs from host
+ *    arrays during the call and keeps no caller pointer after it returns.
+ *  - The context owns its device state: microstructures, the per-qp fluctuation fields
+ *    (current and committed), the macro mesh tables and scratch.  One context may be used
+ *    from one host thread at a time.
+ *  - Calls taking a stream enqueue asynchronous work on it (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream); their outputs are valid once the stream has
+ *    been synchronised.  Argument errors are reported synchronously; CUDA launch errors
+ *    are reported as FEHMM_ERR_CUDA.
+ *  - Micro RVE: the periodic unit cell [0,1]^dim split into n^dim Q1 (dim = 2, plane
+ *    strain) or Hex8 (dim = 3) elements; element (i,j[,k]) has index i + n*j (+ n*n*k);
+ *    node (i,j[,k]) likewise; the fluctuation of node 0 is pinned to zero.
+ *  - Macro mesh: [0,1]^dim split into nx x ny (x nz) Q1/Hex8 elements with 2^dim Gauss
+ *    points; node (i,j[,k]) has index i + (nx+1)*j (+ (nx+1)*(ny+1)*k), dof = node*dim + c;
+ *    quadrature point q = element*2^dim + g with Gauss points ordered xi_1 fastest.
+ */
+#ifndef FEHMM_H
+#define FEHMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fehmm_ctx fehmm_ctx;
+
+enum {
+  FEHMM_OK = 0,
+  FEHMM_ERR_ARG = -1,          /* invalid argument (null pointer, size out of range) */
+  FEHMM_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed */
+  FEHMM_ERR_OOM = -3,          /* device allocation failed */
+  FEHMM_ERR_STATE = -4,        /* call out of order (e.g. solve before bind_qps) */
+  FEHMM_ERR_UNSUPPORTED = -5   /* valid but unsupported configuration (e.g. odd 2D grid) */
+};
+
+enum { FEHMM_PREC_FP64 = 0, FEHMM_PREC_MIXED = 1 };
+
+/* Per-quadrature-point RVE status written by fehmm_rve_solve. */
+enum {
+  FEHMM_RVE_OK = 0,            /* Newton converged */
+  FEHMM_RVE_NEWTON_CAP = 1,    /* iteration cap reached before the tolerance */
+  FEHMM_RVE_J_NONPOS = 2,      /* det F <= 0 at some Gauss point (ln J undefined) */
+  FEHMM_RVE_PCG_BREAKDOWN = 3, /* p^T K p <= 0 in the linear solver (tangent not SPD) */
+  FEHMM_RVE_NONFINITE = 4,     /* NaN/Inf in the residual */
+  FEHMM_RVE_PCG_CAP = 5        /* the tangent-transfer solve hit its iteration cap */
+};
+
+/* fehmm_rve_solve flags */
+enum {
+  FEHMM_SOLVE_NO_TANGENT = 1,     /* skip the condensation: A is not written */
+  FEHMM_SOLVE_FROM_COMMITTED = 2, /* start from the committed fluctuations (first macro
+                                     iteration of a load step, Sec. 5.1 warm start) instead
+                                     of the current ones */
+  FEHMM_SOLVE_ENERGY = 4          /* also write Wbar = <psi> (needs W != NULL) */
+};
+
+typedef struct {
+  int dim;              /* 2 or 3 */
+  int precision;        /* FEHMM_PREC_FP64: every step in FP64.  FEHMM_PREC_MIXED: FP64
+                           residual, Newton test, fluctuation update and homogenised sums;
+                           FP32 tangent and PCG. */
+  double newton_rtol;   /* stop when |R|_2 <= max(newton_rtol*|R_0|_2, newton_atol); R_0 is
+                           the residual at the start of the call */
+  double newton_atol;
+  int max_newton;       /* Newton iterations per call; 1 gives the alternating scheme of
+                           Algorithm 2 (one micro iteration per macro iteration) */
+  double cg_rtol;       /* relative tolerance of the PCG for each Newton correction */
+  int max_cg;
+  double cond_rtol;     /* relative tolerance of the PCG solves of the tangent transfer */
+  int max_cond_cg;
+} fehmm_options;
+
+/* Fill `opt` with defaults for dim (2|3) and precision. */
+int fehmm_default_options(fehmm_options* opt, int dim, int precision);
+
+/* Create a context on the current CUDA device.  opt: host, copied. */
+int fehmm_create(fehmm_ctx** out, const fehmm_options* opt);
+int fehmm_destroy(fehmm_ctx* ctx);
+int fehmm_get_options(const fehmm_ctx* ctx, fehmm_options* opt);
+/* Change tolerances/caps of an existing context (dim and precision must not change). */
+int fehmm_set_options(fehmm_ctx* ctx, const fehmm_options* opt);
+
+/*
+ * Add n_rve microstructures (host arrays, copied).  grid_n[r]: elements per axis of RVE r
+ * (2D: even, 2..32; 3D: see DESIGN).  phase: concatenation of the uint8 phase maps, RVE r
+ * holding grid_n[r]^dim entries in element order.  E, nu: [n_rve][n_phase] per-RVE
+ * material table (Young's modulus, Poisson ratio; Lame constants are derived as in the
+ * paper's Table of material parameters, Sec. 6), n_phase <= 4.  first_id (optional)
+ * receives the id of the first new RVE.  Must precede fehmm_bind_qps.
+ */
+int fehmm_add_rves(fehmm_ctx* ctx, int n_rve, const int32_t* grid_n, const uint8_t* phase,
+                   const double* E, const double* nu, int n_phase, int* first_id);
+
+/*
+ * Bind n_qp macro quadrature points to microstructures (rve_of_qp: host, [n_qp]) and
+ * allocate their fluctuation state (current and committed, both zero).  Replaces any
+ * previous binding.
+ */
+int fehmm_bind_qps(fehmm_ctx* ctx, int n_qp, const int32_t* rve_of_qp);
+
+/*
+ * One batched RVE solve (Sec. 3.3 micro Newton, Eq. Average-of-P-and-F averages and the
+ * tangent transfer of Eq. k-mac-element-6) for every bound quadrature point.
+ *   F      device [n_qp][d*d]   macro deformation gradient Fbar at each point (input)
+ *   P      device [n_qp][d*d]   homogenised Pbar (output)
+ *   A      device [n_qp][d^4]   homogenised tangent dPbar/dFbar (output; may be NULL
+ *                               with FEHMM_SOLVE_NO_TANGENT)
+ *   W      device [n_qp]        <psi> (output, only with FEHMM_SOLVE_ENERGY; else NULL ok)
+ *   status device [n_qp] int32  FEHMM_RVE_* per point (output)
+ *   iters  device [n_qp][4] int32: Newton iterations, PCG iterations of the Newton
+ *          corrections, PCG iterations of the tangent transfer (sum over d*d right-hand
+ *          sides), largest single tangent-transfer PCG count (output; may be NULL)
+ * The fluctuation of each point starts from its current (or, with
+ * FEHMM_SOLVE_FROM_COMMITTED, committed) state and the result becomes the current state.
+ * Returns FEHMM_OK once enqueued; per-point failures are reported through `status`.
+ */
+int fehmm_rve_solve(fehmm_ctx* ctx, const double* F, double* P, double* A, double* W,
+                    int32_t* status, int32_t* iters, int flags, void* stream);
+
+/* Load-step state: commit copies current -> committed fluctuations; rollback the reverse. */
+int fehmm_commit(fehmm_ctx* ctx, void* stream);
+int fehmm_rollback(fehmm_ctx* ctx, void* stream);
+
+/*
+ * Access to the fluctuation of quadrature point q (device pointer to n_node*dim doubles,
+ * node-major, owned by the context, valid until the next bind).  which = 0 current,
+ * 1 committed.  n_values (optional) receives the length.
+ */
+int fehmm_fluctuation(fehmm_ctx* ctx, int q, int which, double** dev_ptr, int* n_values);
+
+/*
+ * Structured macro mesh on [0,1]^dim with n_el[c] elements along axis c (host array of
+ * dim ints).  Builds the CSR pattern of the macro tangent and the colouring of the
+ * assembly.  The number of macro quadrature points is n_el product * 2^dim.
+ */
+int fehmm_macro_create(fehmm_ctx* ctx, const int32_t* n_el);
+
+/* Fbar = I + sum_I u_I (x) Grad N_I at every macro quadrature point (the gradient of
+ * Eq. linearization-uH).  u: device [n_node*dim]; F: device [n_qp][d*d]. */
+int fehmm_macro_qp_F(fehmm_ctx* ctx, const double* u, double* F, void* stream);
+
+/*
+ * Macro residual and tangent (Eq. f_I^int with S^H = <F>^-1<P>, Eq. ModifiedBilinearForm-3,
+ * Eq. Assem_k_T_IK_mac):  f_I = sum_q omega_q Pbar_q Grad N_I,
+ * K_IJ = sum_q omega_q Grad N_I . Abar_q . Grad N_J, omega = Gauss weight * det J.
+ *   P device [n_qp][d*d], A device [n_qp][d^4] (may be NULL: K not assembled),
+ *   f device [n_node*dim] (overwritten), K_vals device [nnz] (overwritten, CSR order of
+ *   fehmm_macro_csr).  No boundary conditions are applied.
+ */
+int fehmm_macro_assemble(fehmm_ctx* ctx, const double* P, const double* A, double* f,
+                         double* K_vals, void* stream);
+
+/* CSR pattern of the macro tangent (device pointers owned by the context). */
+int fehmm_macro_csr(fehmm_ctx* ctx, const int32_t** rowptr, const int32_t** col, int* n_rows,
+                    int* nnz);
+
+/* Number of kernel launches this context has issued since creation (for accounting). */
+long long fehmm_launch_count(const fehmm_ctx* ctx);
+
+const char* fehmm_status_str(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEHMM_H */

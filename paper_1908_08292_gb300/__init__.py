@@ -1,0 +1,239 @@
+"""Python binding of the GB300 batched FE-HMM / FE^2 RVE engine (libfehmm.so, include/fehmm.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  The binding fails loudly when the compiled
+library is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Context", "FehmmError", "lib", "library_path", "PREC_FP64", "PREC_MIXED",
+           "SOLVE_NO_TANGENT", "SOLVE_FROM_COMMITTED", "SOLVE_ENERGY", "RVE_STATUS"]
+
+PREC_FP64, PREC_MIXED = 0, 1
+SOLVE_NO_TANGENT, SOLVE_FROM_COMMITTED, SOLVE_ENERGY = 1, 2, 4
+RVE_STATUS = {0: "ok", 1: "newton_cap", 2: "J<=0", 3: "pcg_breakdown", 4: "nonfinite", 5: "pcg_cap"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libfehmm.so")
+
+
+class FehmmError(RuntimeError):
+    pass
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("precision", ctypes.c_int),
+                ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
+                ("max_newton", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("max_cg", ctypes.c_int),
+                ("cond_rtol", ctypes.c_double), ("max_cond_cg", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "fehmm_default_options": (_I, [ctypes.POINTER(Options), _I, _I]),
+    "fehmm_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Options)]),
+    "fehmm_destroy": (_I, [_P]),
+    "fehmm_get_options": (_I, [_P, ctypes.POINTER(Options)]),
+    "fehmm_set_options": (_I, [_P, ctypes.POINTER(Options)]),
+    "fehmm_add_rves": (_I, [_P, _I, _P, _P, _P, _P, _I, ctypes.POINTER(_I)]),
+    "fehmm_bind_qps": (_I, [_P, _I, _P]),
+    "fehmm_rve_solve": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _P]),
+    "fehmm_commit": (_I, [_P, _P]),
+    "fehmm_rollback": (_I, [_P, _P]),
+    "fehmm_fluctuation": (_I, [_P, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_I)]),
+    "fehmm_macro_create": (_I, [_P, _P]),
+    "fehmm_macro_qp_F": (_I, [_P, _P, _P, _P]),
+    "fehmm_macro_assemble": (_I, [_P, _P, _P, _P, _P, _P]),
+    "fehmm_macro_csr": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "fehmm_launch_count": (ctypes.c_longlong, [_P]),
+    "fehmm_status_str": (ctypes.c_char_p, [_I]),
+}
+
+
+def lib():
+    """Load libfehmm.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise FehmmError(f"{path} is missing: build it with `python -m paper_1908_08292_gb300.build`")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def status_str(code: int) -> str:
+    return lib().fehmm_status_str(int(code)).decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise FehmmError(f"{what}: {status_str(rc)} ({rc})")
+    return rc
+
+
+def _dev(t, dtype, name, numel=None):
+    """Device pointer of a contiguous CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise FehmmError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise FehmmError(f"{name} must be a contiguous {dtype} tensor")
+    if numel is not None and t.numel() < numel:
+        raise FehmmError(f"{name} has {t.numel()} elements, need {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class _DevArray:
+    """__cuda_array_interface__ view of library-owned device memory (no copy)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+class Context:
+    """One fehmm context: microstructures, per-qp fluctuation state and the macro mesh."""
+
+    def __init__(self, dim: int, precision: str = "mixed", **options):
+        L = lib()
+        prec = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
+        opt = Options()
+        _check(L.fehmm_default_options(ctypes.byref(opt), dim, prec), "default_options")
+        for k, v in options.items():
+            if not hasattr(opt, k):
+                raise FehmmError(f"unknown option {k}")
+            setattr(opt, k, v)
+        h = _P()
+        _check(L.fehmm_create(ctypes.byref(h), ctypes.byref(opt)), "create")
+        self._h = h
+        self.dim = dim
+        self.precision = precision
+        self.n_qp = 0
+
+    # -------------------------------------------------------------- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fehmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --------------------------------------------------------------- options
+    @property
+    def options(self) -> Options:
+        opt = Options()
+        _check(lib().fehmm_get_options(self._h, ctypes.byref(opt)), "get_options")
+        return opt
+
+    def set_options(self, **kw):
+        opt = self.options
+        for k, v in kw.items():
+            setattr(opt, k, v)
+        _check(lib().fehmm_set_options(self._h, ctypes.byref(opt)), "set_options")
+
+    # -------------------------------------------------------- microstructure
+    def add_rves(self, grid_n, phases, E, nu) -> int:
+        grid_n = np.ascontiguousarray(grid_n, dtype=np.int32)
+        phase = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.uint8).reshape(-1) for p in phases]))
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        nu = np.ascontiguousarray(nu, dtype=np.float64)
+        if E.ndim != 2 or E.shape != nu.shape or E.shape[0] != grid_n.size:
+            raise FehmmError("E and nu must have shape (n_rve, n_phase)")
+        first = _I()
+        _check(lib().fehmm_add_rves(self._h, int(grid_n.size), grid_n.ctypes.data, phase.ctypes.data,
+                                    E.ctypes.data, nu.ctypes.data, int(E.shape[1]), ctypes.byref(first)),
+               "add_rves")
+        return first.value
+
+    def bind_qps(self, rve_of_qp):
+        r = np.ascontiguousarray(rve_of_qp, dtype=np.int32)
+        _check(lib().fehmm_bind_qps(self._h, int(r.size), r.ctypes.data), "bind_qps")
+        self.n_qp = int(r.size)
+
+    # ------------------------------------------------------------ RVE solves
+    def rve_solve(self, F, P, A=None, status=None, iters=None, W=None, flags=0, stream=None):
+        import torch
+        d, n = self.dim, self.n_qp
+        _check(lib().fehmm_rve_solve(self._h, _dev(F, torch.float64, "F", n * d * d),
+                                     _dev(P, torch.float64, "P", n * d * d),
+                                     _dev(A, torch.float64, "A", n * d ** 4),
+                                     _dev(W, torch.float64, "W", n),
+                                     _dev(status, torch.int32, "status", n),
+                                     _dev(iters, torch.int32, "iters", 4 * n), int(flags), _stream(stream)),
+               "rve_solve")
+
+    def commit(self, stream=None):
+        _check(lib().fehmm_commit(self._h, _stream(stream)), "commit")
+
+    def rollback(self, stream=None):
+        _check(lib().fehmm_rollback(self._h, _stream(stream)), "rollback")
+
+    def fluctuation(self, q: int, committed: bool = False):
+        """Device view (torch float64, no copy) of quadrature point q's fluctuation field."""
+        import torch
+        ptr, n = _P(), _I()
+        _check(lib().fehmm_fluctuation(self._h, int(q), int(committed), ctypes.byref(ptr), ctypes.byref(n)),
+               "fluctuation")
+        return torch.as_tensor(_DevArray(ptr.value, n.value, "<f8"), device="cuda")
+
+    # ------------------------------------------------------------------ macro
+    def macro_create(self, n_el):
+        arr = np.ascontiguousarray(n_el, dtype=np.int32)
+        _check(lib().fehmm_macro_create(self._h, arr.ctypes.data), "macro_create")
+
+    def macro_qp_F(self, u, F, stream=None):
+        import torch
+        _check(lib().fehmm_macro_qp_F(self._h, _dev(u, torch.float64, "u"), _dev(F, torch.float64, "F"),
+                                      _stream(stream)), "macro_qp_F")
+
+    def macro_assemble(self, P, A, f, K_vals, stream=None):
+        import torch
+        _check(lib().fehmm_macro_assemble(self._h, _dev(P, torch.float64, "P"), _dev(A, torch.float64, "A"),
+                                          _dev(f, torch.float64, "f"), _dev(K_vals, torch.float64, "K_vals"),
+                                          _stream(stream)), "macro_assemble")
+
+    def macro_csr(self):
+        """(rowptr, col, n_rows, nnz); rowptr/col are int32 device views owned by the context."""
+        import torch
+        rp, cl, nr, nz = _P(), _P(), _I(), _I()
+        _check(lib().fehmm_macro_csr(self._h, ctypes.byref(rp), ctypes.byref(cl), ctypes.byref(nr), ctypes.byref(nz)),
+               "macro_csr")
+        rowptr = torch.as_tensor(_DevArray(rp.value, nr.value + 1, "<i4"), device="cuda")
+        col = torch.as_tensor(_DevArray(cl.value, nz.value, "<i4"), device="cuda")
+        return rowptr, col, nr.value, nz.value
+
+    @property
+    def launches(self) -> int:
+        return int(lib().fehmm_launch_count(self._h))

@@ -1,0 +1,462 @@
+// C ABI of the batched FE-HMM RVE engine (declarations and contracts in include/fehmm.h).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <new>
+#include <vector>
+
+#include "fehmm.h"
+#include "fehmm_device.cuh"
+#include "rve_args.h"
+
+using namespace fehmm;
+
+struct fehmm_ctx {
+  fehmm_options opt;
+  int device = 0, num_sms = 0;
+  // microstructures (host copies; device copies rebuilt on bind)
+  std::vector<int32_t> rve_n;
+  std::vector<int64_t> rve_phase_off;
+  std::vector<uint8_t> phase;
+  std::vector<double> lame;  // [n_rve][kMaxPhase][2]
+  int32_t* d_rve_n = nullptr;
+  int64_t* d_rve_phase_off = nullptr;
+  uint8_t* d_phase = nullptr;
+  double* d_lame = nullptr;
+  // quadrature points
+  int n_qp = 0, nn_max = 0;
+  size_t w_total = 0;
+  std::vector<int64_t> w_off_h;
+  int32_t* d_qp_rve = nullptr;
+  int32_t* d_order = nullptr;
+  int64_t* d_w_off = nullptr;
+  double* d_w_cur = nullptr;
+  double* d_w_comm = nullptr;
+  int32_t* d_queue = nullptr;
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // macro mesh
+  bool has_macro = false;
+  MacroArgs macro{};
+  int32_t* d_rowptr = nullptr;
+  int32_t* d_col = nullptr;
+  int32_t* d_blk_base = nullptr;
+  int32_t* d_blk_stride = nullptr;
+  int macro_rows = 0, macro_nnz = 0;
+  long long launches = 0;
+};
+
+namespace {
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+template <typename T>
+int dupload(T*& dst, const T* src, size_t count) {
+  dfree(dst);
+  if (count == 0) return FEHMM_OK;
+  if (cudaMalloc((void**)&dst, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    dst = nullptr;
+    return FEHMM_ERR_OOM;
+  }
+  if (cudaMemcpy(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice) != cudaSuccess) return FEHMM_ERR_CUDA;
+  return FEHMM_OK;
+}
+
+bool valid_options(const fehmm_options* o) {
+  return o && (o->dim == 2 || o->dim == 3) && (o->precision == FEHMM_PREC_FP64 || o->precision == FEHMM_PREC_MIXED) &&
+         o->newton_rtol >= 0 && o->newton_atol >= 0 && o->max_newton >= 0 && o->cg_rtol > 0 && o->max_cg > 0 &&
+         o->cond_rtol > 0 && o->max_cond_cg > 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fehmm_default_options(fehmm_options* opt, int dim, int precision) {
+  if (!opt || (dim != 2 && dim != 3) || (precision != FEHMM_PREC_FP64 && precision != FEHMM_PREC_MIXED))
+    return FEHMM_ERR_ARG;
+  opt->dim = dim;
+  opt->precision = precision;
+  opt->newton_rtol = 1e-10;
+  opt->newton_atol = 1e-14;
+  opt->max_newton = 25;
+  opt->cg_rtol = precision == FEHMM_PREC_FP64 ? 1e-6 : 1e-4;
+  opt->max_cg = 2000;
+  opt->cond_rtol = precision == FEHMM_PREC_FP64 ? 1e-9 : 1e-5;
+  opt->max_cond_cg = 4000;
+  return FEHMM_OK;
+}
+
+int fehmm_create(fehmm_ctx** out, const fehmm_options* opt) {
+  if (!out || !valid_options(opt)) return FEHMM_ERR_ARG;
+  *out = nullptr;
+  fehmm_ctx* c = new (std::nothrow) fehmm_ctx();
+  if (!c) return FEHMM_ERR_OOM;
+  c->opt = *opt;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return FEHMM_ERR_CUDA;
+  }
+  if (cudaMalloc((void**)&c->d_queue, sizeof(int32_t) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return FEHMM_ERR_OOM;
+  }
+  *out = c;
+  return FEHMM_OK;
+}
+
+int fehmm_destroy(fehmm_ctx* c) {
+  if (!c) return FEHMM_ERR_ARG;
+  dfree(c->d_rve_n);
+  dfree(c->d_rve_phase_off);
+  dfree(c->d_phase);
+  dfree(c->d_lame);
+  dfree(c->d_qp_rve);
+  dfree(c->d_order);
+  dfree(c->d_w_off);
+  dfree(c->d_w_cur);
+  dfree(c->d_w_comm);
+  dfree(c->d_queue);
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  dfree(c->d_rowptr);
+  dfree(c->d_col);
+  dfree(c->d_blk_base);
+  dfree(c->d_blk_stride);
+  delete c;
+  return FEHMM_OK;
+}
+
+int fehmm_get_options(const fehmm_ctx* c, fehmm_options* opt) {
+  if (!c || !opt) return FEHMM_ERR_ARG;
+  *opt = c->opt;
+  return FEHMM_OK;
+}
+
+int fehmm_set_options(fehmm_ctx* c, const fehmm_options* opt) {
+  if (!c || !valid_options(opt) || opt->dim != c->opt.dim || opt->precision != c->opt.precision) return FEHMM_ERR_ARG;
+  c->opt = *opt;
+  return FEHMM_OK;
+}
+
+int fehmm_add_rves(fehmm_ctx* c, int n_rve, const int32_t* grid_n, const uint8_t* phase, const double* E,
+                   const double* nu, int n_phase, int* first_id) {
+  if (!c || n_rve <= 0 || !grid_n || !phase || !E || !nu || n_phase <= 0 || n_phase > kMaxPhase) return FEHMM_ERR_ARG;
+  const int d = c->opt.dim;
+  for (int r = 0; r < n_rve; ++r) {
+    const int n = grid_n[r];
+    if (d == 2 && (n < 2 || n > 32)) return FEHMM_ERR_ARG;
+    if (d == 2 && (n % 2) != 0) return FEHMM_ERR_UNSUPPORTED;
+    if (d == 3) return FEHMM_ERR_UNSUPPORTED;
+    for (int p = 0; p < n_phase; ++p) {
+      const double e = E[(size_t)r * n_phase + p], v = nu[(size_t)r * n_phase + p];
+      if (!(e > 0) || !(v > -1.0 && v < 0.5)) return FEHMM_ERR_ARG;
+    }
+  }
+  // validate phase ids before touching the context
+  size_t off = 0;
+  for (int r = 0; r < n_rve; ++r) {
+    size_t cnt = 1;
+    for (int k = 0; k < d; ++k) cnt *= (size_t)grid_n[r];
+    for (size_t i = 0; i < cnt; ++i)
+      if (phase[off + i] >= n_phase) return FEHMM_ERR_ARG;
+    off += cnt;
+  }
+  if (first_id) *first_id = (int)c->rve_n.size();
+  off = 0;
+  for (int r = 0; r < n_rve; ++r) {
+    size_t cnt = 1;
+    for (int k = 0; k < d; ++k) cnt *= (size_t)grid_n[r];
+    c->rve_n.push_back(grid_n[r]);
+    c->rve_phase_off.push_back((int64_t)c->phase.size());
+    c->phase.insert(c->phase.end(), phase + off, phase + off + cnt);
+    off += cnt;
+    for (int p = 0; p < kMaxPhase; ++p) {
+      double lam = 0, mu = 0;
+      if (p < n_phase) lame_from_E_nu(E[(size_t)r * n_phase + p], nu[(size_t)r * n_phase + p], lam, mu);
+      c->lame.push_back(lam);
+      c->lame.push_back(mu);
+    }
+  }
+  return FEHMM_OK;
+}
+
+int fehmm_bind_qps(fehmm_ctx* c, int n_qp, const int32_t* rve_of_qp) {
+  if (!c || n_qp <= 0 || !rve_of_qp) return FEHMM_ERR_ARG;
+  if (c->rve_n.empty()) return FEHMM_ERR_STATE;
+  const int n_rve = (int)c->rve_n.size(), d = c->opt.dim;
+  for (int q = 0; q < n_qp; ++q)
+    if (rve_of_qp[q] < 0 || rve_of_qp[q] >= n_rve) return FEHMM_ERR_ARG;
+  int rc;
+  if ((rc = dupload(c->d_rve_n, c->rve_n.data(), c->rve_n.size())) ||
+      (rc = dupload(c->d_rve_phase_off, c->rve_phase_off.data(), c->rve_phase_off.size())) ||
+      (rc = dupload(c->d_phase, c->phase.data(), c->phase.size())) ||
+      (rc = dupload(c->d_lame, c->lame.data(), c->lame.size())))
+    return rc;
+  std::vector<int64_t> off(n_qp);
+  size_t total = 0;
+  int nn_max = 0;
+  std::vector<int> nodes(n_qp);
+  for (int q = 0; q < n_qp; ++q) {
+    const int n = c->rve_n[rve_of_qp[q]];
+    int nn = 1;
+    for (int k = 0; k < d; ++k) nn *= n;
+    nodes[q] = nn;
+    nn_max = std::max(nn_max, nn);
+    off[q] = (int64_t)total;
+    total += (size_t)nn * d;
+  }
+  // largest RVEs first so the persistent blocks finish together
+  std::vector<int32_t> order(n_qp);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nodes[a] > nodes[b]; });
+  if ((rc = dupload(c->d_qp_rve, rve_of_qp, (size_t)n_qp)) || (rc = dupload(c->d_order, order.data(), order.size())) ||
+      (rc = dupload(c->d_w_off, off.data(), off.size())))
+    return rc;
+  dfree(c->d_w_cur);
+  dfree(c->d_w_comm);
+  if (cudaMalloc((void**)&c->d_w_cur, sizeof(double) * total) != cudaSuccess ||
+      cudaMalloc((void**)&c->d_w_comm, sizeof(double) * total) != cudaSuccess) {
+    cudaGetLastError();
+    dfree(c->d_w_cur);
+    dfree(c->d_w_comm);
+    c->n_qp = 0;
+    return FEHMM_ERR_OOM;
+  }
+  if (cudaMemset(c->d_w_cur, 0, sizeof(double) * total) != cudaSuccess ||
+      cudaMemset(c->d_w_comm, 0, sizeof(double) * total) != cudaSuccess)
+    return FEHMM_ERR_CUDA;
+  const int blocks = std::min(n_qp, c->num_sms);
+  const size_t sb = rve2d_scratch_bytes(nn_max, c->opt.precision == FEHMM_PREC_MIXED, blocks);
+  if (sb > c->scratch_bytes) {
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    c->d_scratch = nullptr;
+    c->scratch_bytes = 0;
+    if (cudaMalloc(&c->d_scratch, sb) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_scratch = nullptr;
+      return FEHMM_ERR_OOM;
+    }
+    c->scratch_bytes = sb;
+  }
+  c->n_qp = n_qp;
+  c->nn_max = nn_max;
+  c->w_total = total;
+  c->w_off_h = off;
+  return FEHMM_OK;
+}
+
+int fehmm_rve_solve(fehmm_ctx* c, const double* F, double* P, double* A, double* W, int32_t* status, int32_t* iters,
+                    int flags, void* stream) {
+  if (!c || !F || !P || !status) return FEHMM_ERR_ARG;
+  if (!(flags & FEHMM_SOLVE_NO_TANGENT) && !A) return FEHMM_ERR_ARG;
+  if ((flags & FEHMM_SOLVE_ENERGY) && !W) return FEHMM_ERR_ARG;
+  if (c->n_qp <= 0) return FEHMM_ERR_STATE;
+  if (c->opt.dim != 2) return FEHMM_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  Rve2dArgs a{};
+  a.n_qp = c->n_qp;
+  a.nn_max = c->nn_max;
+  a.order = c->d_order;
+  a.qp_rve = c->d_qp_rve;
+  a.rve_n = c->d_rve_n;
+  a.rve_phase_off = c->d_rve_phase_off;
+  a.phase = c->d_phase;
+  a.rve_lame = c->d_lame;
+  a.qp_w_off = c->d_w_off;
+  a.w_in = (flags & FEHMM_SOLVE_FROM_COMMITTED) ? c->d_w_comm : c->d_w_cur;
+  a.w_out = c->d_w_cur;
+  a.F = F;
+  a.P = P;
+  a.A = (flags & FEHMM_SOLVE_NO_TANGENT) ? nullptr : A;
+  a.W = W;
+  a.status = status;
+  a.iters = iters;
+  a.queue = c->d_queue;
+  a.scratch = c->d_scratch;
+  a.newton_rtol = c->opt.newton_rtol;
+  a.newton_atol = c->opt.newton_atol;
+  a.cg_rtol = c->opt.cg_rtol;
+  a.cond_rtol = c->opt.cond_rtol;
+  a.max_newton = c->opt.max_newton;
+  a.max_cg = c->opt.max_cg;
+  a.max_cond_cg = c->opt.max_cond_cg;
+  a.flags = flags;
+  if (cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;
+  const int blocks = std::min(c->n_qp, c->num_sms);
+  if (rve2d_launch(a, c->opt.precision == FEHMM_PREC_MIXED, blocks, s) != cudaSuccess) return FEHMM_ERR_CUDA;
+  c->launches += 1;
+  return FEHMM_OK;
+}
+
+int fehmm_commit(fehmm_ctx* c, void* stream) {
+  if (!c) return FEHMM_ERR_ARG;
+  if (c->n_qp <= 0) return FEHMM_ERR_STATE;
+  return cudaMemcpyAsync(c->d_w_comm, c->d_w_cur, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice,
+                         (cudaStream_t)stream) == cudaSuccess
+             ? FEHMM_OK
+             : FEHMM_ERR_CUDA;
+}
+
+int fehmm_rollback(fehmm_ctx* c, void* stream) {
+  if (!c) return FEHMM_ERR_ARG;
+  if (c->n_qp <= 0) return FEHMM_ERR_STATE;
+  return cudaMemcpyAsync(c->d_w_cur, c->d_w_comm, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice,
+                         (cudaStream_t)stream) == cudaSuccess
+             ? FEHMM_OK
+             : FEHMM_ERR_CUDA;
+}
+
+int fehmm_fluctuation(fehmm_ctx* c, int q, int which, double** dev_ptr, int* n_values) {
+  if (!c || !dev_ptr || q < 0 || q >= c->n_qp || (which != 0 && which != 1)) return FEHMM_ERR_ARG;
+  *dev_ptr = (which ? c->d_w_comm : c->d_w_cur) + c->w_off_h[q];
+  if (n_values) {
+    const size_t end = (q + 1 < c->n_qp) ? (size_t)c->w_off_h[q + 1] : c->w_total;
+    *n_values = (int)(end - (size_t)c->w_off_h[q]);
+  }
+  return FEHMM_OK;
+}
+
+int fehmm_macro_create(fehmm_ctx* c, const int32_t* n_el) {
+  if (!c || !n_el) return FEHMM_ERR_ARG;
+  const int d = c->opt.dim;
+  for (int k = 0; k < d; ++k)
+    if (n_el[k] < 1 || n_el[k] > 4096) return FEHMM_ERR_ARG;
+  MacroArgs m{};
+  m.dim = d;
+  int nx[3] = {1, 1, 1};
+  for (int k = 0; k < d; ++k) {
+    nx[k] = n_el[k];
+    m.nel[k] = n_el[k];
+    m.h[k] = 1.0 / n_el[k];
+  }
+  m.nen = 1 << d;
+  m.nq = 1 << d;
+  m.n_el = nx[0] * nx[1] * nx[2];
+  const int N0 = nx[0] + 1, N1 = nx[1] + 1, N2 = d == 3 ? nx[2] + 1 : 1;
+  m.n_nodes = N0 * N1 * N2;
+  m.n_qp = m.n_el * m.nq;
+  // node-neighbour CSR (3^d stencil clipped at the boundary), d x d blocks
+  const int nn = m.n_nodes;
+  std::vector<std::vector<int>> nbr(nn);
+  for (int k = 0; k < N2; ++k)
+    for (int j = 0; j < N1; ++j)
+      for (int i = 0; i < N0; ++i) {
+        const int I = i + N0 * (j + N1 * k);
+        for (int dk = (d == 3 ? -1 : 0); dk <= (d == 3 ? 1 : 0); ++dk)
+          for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+              const int ii = i + di, jj = j + dj, kk = k + dk;
+              if (ii < 0 || jj < 0 || kk < 0 || ii >= N0 || jj >= N1 || kk >= N2) continue;
+              nbr[I].push_back(ii + N0 * (jj + N1 * kk));
+            }
+        std::sort(nbr[I].begin(), nbr[I].end());
+      }
+  std::vector<int32_t> rowptr((size_t)nn * d + 1, 0), col;
+  std::vector<int32_t> node_base(nn);
+  size_t pos = 0;
+  for (int I = 0; I < nn; ++I) {
+    node_base[I] = (int32_t)pos;
+    for (int i = 0; i < d; ++i) {
+      rowptr[(size_t)I * d + i] = (int32_t)pos;
+      for (int J : nbr[I])
+        for (int k = 0; k < d; ++k) col.push_back(J * d + k);
+      pos += nbr[I].size() * d;
+    }
+  }
+  rowptr[(size_t)nn * d] = (int32_t)pos;
+  if (pos > (size_t)INT32_MAX) return FEHMM_ERR_UNSUPPORTED;
+  const int nen = m.nen;
+  std::vector<int32_t> blk_base((size_t)m.n_el * nen * nen), blk_stride((size_t)m.n_el * nen);
+  auto corner = [&](int e, int a) {
+    const int ex = e % nx[0], ey = (e / nx[0]) % nx[1], ez = e / (nx[0] * nx[1]);
+    const int ox = ((a & 3) == 1 || (a & 3) == 2), oy = (a & 3) >= 2, oz = a >= 4;
+    return (ex + ox) + N0 * ((ey + oy) + N1 * (ez + oz));
+  };
+  for (int e = 0; e < m.n_el; ++e)
+    for (int I = 0; I < nen; ++I) {
+      const int nI = corner(e, I);
+      blk_stride[(size_t)e * nen + I] = (int32_t)(nbr[nI].size() * d);
+      for (int J = 0; J < nen; ++J) {
+        const int nJ = corner(e, J);
+        const int rank = (int)(std::lower_bound(nbr[nI].begin(), nbr[nI].end(), nJ) - nbr[nI].begin());
+        blk_base[((size_t)e * nen + I) * nen + J] = node_base[nI] + rank * d;
+      }
+    }
+  int rc;
+  if ((rc = dupload(c->d_rowptr, rowptr.data(), rowptr.size())) || (rc = dupload(c->d_col, col.data(), col.size())) ||
+      (rc = dupload(c->d_blk_base, blk_base.data(), blk_base.size())) ||
+      (rc = dupload(c->d_blk_stride, blk_stride.data(), blk_stride.size())))
+    return rc;
+  m.blk_base = c->d_blk_base;
+  m.blk_stride = c->d_blk_stride;
+  c->macro = m;
+  c->macro_rows = nn * d;
+  c->macro_nnz = (int)pos;
+  c->has_macro = true;
+  return FEHMM_OK;
+}
+
+int fehmm_macro_qp_F(fehmm_ctx* c, const double* u, double* F, void* stream) {
+  if (!c || !u || !F) return FEHMM_ERR_ARG;
+  if (!c->has_macro) return FEHMM_ERR_STATE;
+  MacroArgs m = c->macro;
+  m.u = u;
+  m.F = F;
+  if (macro_qp_F_launch(m, (cudaStream_t)stream) != cudaSuccess) return FEHMM_ERR_CUDA;
+  c->launches += 1;
+  return FEHMM_OK;
+}
+
+int fehmm_macro_assemble(fehmm_ctx* c, const double* P, const double* A, double* f, double* K_vals, void* stream) {
+  if (!c || !P || !f || (A && !K_vals)) return FEHMM_ERR_ARG;
+  if (!c->has_macro) return FEHMM_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  MacroArgs m = c->macro;
+  m.P = P;
+  m.A = A;
+  m.f = f;
+  m.K = K_vals;
+  if (cudaMemsetAsync(f, 0, sizeof(double) * (size_t)m.n_nodes * m.dim, s) != cudaSuccess) return FEHMM_ERR_CUDA;
+  if (A && cudaMemsetAsync(K_vals, 0, sizeof(double) * (size_t)c->macro_nnz, s) != cudaSuccess) return FEHMM_ERR_CUDA;
+  int launches = 0;
+  const cudaError_t err = macro_assemble_launch(m, s, &launches);
+  c->launches += launches;
+  return err == cudaSuccess ? FEHMM_OK : FEHMM_ERR_CUDA;
+}
+
+int fehmm_macro_csr(fehmm_ctx* c, const int32_t** rowptr, const int32_t** col, int* n_rows, int* nnz) {
+  if (!c) return FEHMM_ERR_ARG;
+  if (!c->has_macro) return FEHMM_ERR_STATE;
+  if (rowptr) *rowptr = c->d_rowptr;
+  if (col) *col = c->d_col;
+  if (n_rows) *n_rows = c->macro_rows;
+  if (nnz) *nnz = c->macro_nnz;
+  return FEHMM_OK;
+}
+
+long long fehmm_launch_count(const fehmm_ctx* c) { return c ? c->launches : -1; }
+
+const char* fehmm_status_str(int code) {
+  switch (code) {
+    case FEHMM_OK: return "ok";
+    case FEHMM_ERR_ARG: return "invalid argument";
+    case FEHMM_ERR_CUDA: return "CUDA error";
+    case FEHMM_ERR_OOM: return "out of device memory";
+    case FEHMM_ERR_STATE: return "call out of order";
+    case FEHMM_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return code > 0 ? "some RVE solves did not converge" : "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,812 @@
+// Batched periodic-RVE Newton solver for 2D plane strain (Q1, 2x2 Gauss), one thread
+// block per RVE, persistent over a work queue of macro quadrature points.
+//
+// Method (paper Sec. 3.2-3.3): for each macro quadrature point the fluctuation w of the
+// periodic RVE solves R(w) = 0 with R_a = sum_e sum_qp wt detJ P(Fbar + Grad w) Grad N_a
+// (Eq. f_I^int on the micro scale); Newton corrections solve K_T dw = -R (Eq.
+// Saddlepoint-problem-Set-of-eqs with the periodic constraints eliminated, ch_3_eq_19-1,
+// ch_3_eq_22).  The outputs are Pbar = <P> (Eq. Average-of-P-and-F) and the tangent
+// transfer Abar_(c)(c') = <(E_c + Grad X_c) : A : (E_c' + Grad X_c')>, where X_c are the
+// periodic responses to the unit macro gradients E_c; this is the paper's
+// k^H = omega/|K_delta| T^T K_T T (Eq. k-mac-element-6/7) written per unit gradient.
+//
+// GB300 layout (one RVE per SM, everything on chip):
+//  * 512 threads; thread (col, strip) owns the node pair (col, 2*strip), (col, 2*strip+1)
+//    and the two elements whose lower-left corners are those nodes.
+//  * w (FP64) lives in shared memory; the residual is evaluated per element in FP64 and the
+//    element forces are staged in shared memory, then gathered per node (no atomics).
+//  * Mixed precision (TA = float): element tangents are staged in shared memory and the
+//    assembled 9-point block stencil of each owned node (9 x 2x2 floats) is gathered into
+//    REGISTERS, where it stays for the whole PCG; the PCG exchanges only the search
+//    direction through shared memory.  FP64 mode (TA = double) keeps the staged element
+//    tangents and the stencil in a per-block global scratch area (L2 resident).
+//  * Block-Jacobi preconditioner (inverted 2x2 nodal diagonal blocks).
+//  * Newton iterations stop on the FP64 2-norm of the residual; PCG inner products are
+//    summed in TA (see DESIGN for the measured FP64/FP32 rate that motivates it).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "fehmm_device.cuh"
+#include "rve_args.h"
+
+namespace fehmm {
+
+namespace {
+
+constexpr int kThreads2D = 512;
+
+__host__ __device__ constexpr int offx(int a) { return (a == 1 || a == 2) ? 1 : 0; }
+__host__ __device__ constexpr int offy(int a) { return a >= 2 ? 1 : 0; }
+// upper-triangle index of a symmetric 8x8 element matrix
+__host__ __device__ constexpr int tri8(int r, int c) {
+  return r <= c ? r * 8 - (r * (r - 1)) / 2 + (c - r) : c * 8 - (c * (c - 1)) / 2 + (r - c);
+}
+
+__device__ __forceinline__ double gauss01(int g) {
+  // Gauss points of [0,1]: 1/2 -+ 1/(2 sqrt 3)
+  return g == 0 ? 0.21132486540518711775 : 0.78867513459481288225;
+}
+
+template <typename TA>
+struct Smem2D {
+  double2* w;        // [NN] fluctuation (FP64)
+  float2* w32;       // [NN] FP32 copy (mixed mode only)
+  vec2_t<TA>* p;     // [NN] PCG search direction
+  unsigned char* stage;  // element forces / element tangents / condensation solutions
+  double* red;       // 2 x 512 doubles of reduction buffers
+  double* lame;      // [kMaxPhase][2]
+};
+
+template <typename TA>
+__host__ __device__ inline size_t smem2d_layout(int NN, Smem2D<TA>* s, unsigned char* base) {
+  constexpr bool REG = std::is_same<TA, float>::value;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 15) & ~size_t(15);
+    return o;
+  };
+  size_t o_w = take(sizeof(double2) * NN);
+  size_t o_w32 = REG ? take(sizeof(float2) * NN) : 0;
+  size_t o_p = take(sizeof(vec2_t<TA>) * NN);
+  size_t stage_bytes = sizeof(double) * 8 * NN;                               // element forces
+  if (REG && sizeof(float) * 36 * NN > stage_bytes) stage_bytes = sizeof(float) * 36 * NN;  // Ke
+  if (sizeof(vec2_t<TA>) * 4 * NN > stage_bytes) stage_bytes = sizeof(vec2_t<TA>) * 4 * NN;  // X
+  size_t o_stage = take(stage_bytes);
+  size_t o_red = take(sizeof(double) * 2 * 512);
+  size_t o_lame = take(sizeof(double) * 2 * kMaxPhase);
+  if (s) {
+    s->w = reinterpret_cast<double2*>(base + o_w);
+    s->w32 = REG ? reinterpret_cast<float2*>(base + o_w32) : nullptr;
+    s->p = reinterpret_cast<vec2_t<TA>*>(base + o_p);
+    s->stage = base + o_stage;
+    s->red = reinterpret_cast<double*>(base + o_red);
+    s->lame = reinterpret_cast<double*>(base + o_lame);
+  }
+  return off;
+}
+
+// Per-thread geometry of the owned node pair.
+struct Own2D {
+  int n, NN, col, strip;
+  bool active;
+  int node[2];   // (col, 2*strip), (col, 2*strip+1)
+  int rows[4];   // 2s-1, 2s, 2s+1, 2s+2 (periodic)
+  int cols[3];   // col-1, col, col+1 (periodic)
+};
+
+__device__ __forceinline__ Own2D make_own(int n) {
+  Own2D o;
+  o.n = n;
+  o.NN = n * n;
+  const int t = threadIdx.x;
+  o.col = t % n;
+  o.strip = t / n;
+  o.active = o.strip < n / 2;
+  const int r0 = 2 * o.strip;
+  o.node[0] = o.col + n * r0;
+  o.node[1] = o.node[0] + n;
+  o.rows[0] = (r0 - 1 + n) % n;
+  o.rows[1] = r0;
+  o.rows[2] = (r0 + 1) % n;
+  o.rows[3] = (r0 + 2) % n;
+  o.cols[0] = (o.col - 1 + n) % n;
+  o.cols[1] = o.col;
+  o.cols[2] = (o.col + 1) % n;
+  return o;
+}
+
+// Stencil storage: REG -> K[2][9][4] registers; else global scratch [36][NN].
+template <typename TA, bool REG>
+struct Stencil {
+  TA K[2][9][4];
+  TA* g;  // global stencil base (FP64 mode)
+  int NN;
+  __device__ __forceinline__ TA get(int s, int nb, int c, int node) const {
+    if constexpr (REG) {
+      return K[s][nb][c];
+    } else {
+      return g[(size_t)(nb * 4 + c) * NN + node];
+    }
+  }
+};
+
+// ------------------------------------------------------------------ residual (FP64)
+// Element e's nodal forces into stage[k][e] (k = 2*local_node + comp) and this thread's
+// contributions to sum wt P and to the J <= 0 flag.
+__device__ __forceinline__ void element_residual(int e, int n, const double2* w, const double* Fb,
+                                                 double lam, double mu, double* stage_f, double (&Psum)[4],
+                                                 double& bad) {
+  const int i = e % n, j = e / n, ip = (i + 1) % n, jp = (j + 1) % n;
+  const double2 w0 = w[e], w1 = w[ip + n * j], w2 = w[ip + n * jp], w3 = w[i + n * jp];
+  const double ih = (double)n;
+  const double2 d10 = make_double2(w1.x - w0.x, w1.y - w0.y);
+  const double2 d30 = make_double2(w3.x - w0.x, w3.y - w0.y);
+  const double2 e1 = make_double2((w2.x - w3.x) - d10.x, (w2.y - w3.y) - d10.y);
+  const double2 e2 = make_double2((w2.x - w1.x) - d30.x, (w2.y - w1.y) - d30.y);
+  double Sa0x = 0, Sa0y = 0, Sa1x = 0, Sa1y = 0, Sb0x = 0, Sb0y = 0, Sb1x = 0, Sb1y = 0;
+#pragma unroll
+  for (int gy = 0; gy < 2; ++gy) {
+    const double t = gauss01(gy);
+#pragma unroll
+    for (int gx = 0; gx < 2; ++gx) {
+      const double s = gauss01(gx);
+      const double F00 = fma(ih, fma(t, e1.x, d10.x), Fb[0]);
+      const double F10 = fma(ih, fma(t, e1.y, d10.y), Fb[2]);
+      const double F01 = fma(ih, fma(s, e2.x, d30.x), Fb[1]);
+      const double F11 = fma(ih, fma(s, e2.y, d30.y), Fb[3]);
+      const NH2<double> q = nh2_eval(F00, F01, F10, F11, lam, mu);
+      bad += (q.J > 0.0) ? 0.0 : 1.0;
+      const double P00 = fma(mu, F00, q.hb * q.f00), P01 = fma(mu, F01, q.hb * q.f01);
+      const double P10 = fma(mu, F10, q.hb * q.f10), P11 = fma(mu, F11, q.hb * q.f11);
+      Psum[0] += P00;
+      Psum[1] += P01;
+      Psum[2] += P10;
+      Psum[3] += P11;
+      Sa0x = fma(1.0 - t, P00, Sa0x);
+      Sa0y = fma(1.0 - t, P10, Sa0y);
+      Sa1x = fma(t, P00, Sa1x);
+      Sa1y = fma(t, P10, Sa1y);
+      Sb0x = fma(1.0 - s, P01, Sb0x);
+      Sb0y = fma(1.0 - s, P11, Sb0y);
+      Sb1x = fma(s, P01, Sb1x);
+      Sb1y = fma(s, P11, Sb1y);
+    }
+  }
+  // R_a = (wq / h) P G_a with wq = h^2/4 and G_a the natural-coordinate gradients.
+  const double k = 0.25 / ih;
+  const int NN = n * n;
+  stage_f[0 * NN + e] = k * (-Sa0x - Sb0x);
+  stage_f[1 * NN + e] = k * (-Sa0y - Sb0y);
+  stage_f[2 * NN + e] = k * (Sa0x - Sb1x);
+  stage_f[3 * NN + e] = k * (Sa0y - Sb1y);
+  stage_f[4 * NN + e] = k * (Sa1x + Sb1x);
+  stage_f[5 * NN + e] = k * (Sa1y + Sb1y);
+  stage_f[6 * NN + e] = k * (-Sa1x + Sb0x);
+  stage_f[7 * NN + e] = k * (-Sa1y + Sb0y);
+}
+
+// Psi = lam/4 (J^2-1) - (lam/2+mu) ln J + mu/2 (|F|^2 - 2) summed over the element's Gauss points.
+__device__ __forceinline__ double element_energy(int e, int n, const double2* w, const double* Fb, double lam,
+                                                 double mu) {
+  const int i = e % n, j = e / n, ip = (i + 1) % n, jp = (j + 1) % n;
+  const double2 w0 = w[e], w1 = w[ip + n * j], w2 = w[ip + n * jp], w3 = w[i + n * jp];
+  const double ih = (double)n;
+  double acc = 0.0;
+#pragma unroll
+  for (int gy = 0; gy < 2; ++gy) {
+    const double t = gauss01(gy);
+#pragma unroll
+    for (int gx = 0; gx < 2; ++gx) {
+      const double s = gauss01(gx);
+      const double F00 = Fb[0] + ih * ((1 - t) * (w1.x - w0.x) + t * (w2.x - w3.x));
+      const double F10 = Fb[2] + ih * ((1 - t) * (w1.y - w0.y) + t * (w2.y - w3.y));
+      const double F01 = Fb[1] + ih * ((1 - s) * (w3.x - w0.x) + s * (w2.x - w1.x));
+      const double F11 = Fb[3] + ih * ((1 - s) * (w3.y - w0.y) + s * (w2.y - w1.y));
+      const double J = F00 * F11 - F01 * F10;
+      const double trC = F00 * F00 + F01 * F01 + F10 * F10 + F11 * F11;
+      acc += 0.25 * lam * (J * J - 1.0) - (0.5 * lam + mu) * log(J) + 0.5 * mu * (trC - 2.0);
+    }
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------------ tangent (TA)
+// Element tangent Ke (36 upper-triangle entries) into stage[tri][slot].
+template <typename TA>
+__device__ __forceinline__ void element_tangent(int e, int n, const vec2_t<TA>* w, const TA* Fb, TA lam, TA mu,
+                                                TA* stage_k, int slot, int NN) {
+  const int i = e % n, j = e / n, ip = (i + 1) % n, jp = (j + 1) % n;
+  const vec2_t<TA> w0 = w[e], w1 = w[ip + n * j], w2 = w[ip + n * jp], w3 = w[i + n * jp];
+  const TA ih = (TA)n;
+  const TA d10x = w1.x - w0.x, d10y = w1.y - w0.y, d30x = w3.x - w0.x, d30y = w3.y - w0.y;
+  const TA e1x = (w2.x - w3.x) - d10x, e1y = (w2.y - w3.y) - d10y;
+  const TA e2x = (w2.x - w1.x) - d30x, e2y = (w2.y - w1.y) - d30y;
+  TA Ke[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) Ke[k] = TA(0);
+  const TA wq = TA(0.25) / (ih * ih);
+#pragma unroll
+  for (int gy = 0; gy < 2; ++gy) {
+    const TA t = (TA)gauss01(gy);
+#pragma unroll
+    for (int gx = 0; gx < 2; ++gx) {
+      const TA s = (TA)gauss01(gx);
+      const TA F00 = Fb[0] + ih * (d10x + t * e1x);
+      const TA F10 = Fb[2] + ih * (d10y + t * e1y);
+      const TA F01 = Fb[1] + ih * (d30x + s * e2x);
+      const TA F11 = Fb[3] + ih * (d30y + s * e2y);
+      const NH2<TA> q = nh2_eval(F00, F01, F10, F11, lam, mu);
+      // physical shape gradients g_a and v_a = Fit g_a
+      TA gx_[4] = {-(1 - t) * ih, (1 - t) * ih, t * ih, -t * ih};
+      TA gy_[4] = {-(1 - s) * ih, -s * ih, s * ih, (1 - s) * ih};
+      TA vx[4], vy[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        vx[a] = q.f00 * gx_[a] + q.f01 * gy_[a];
+        vy[a] = q.f10 * gx_[a] + q.f11 * gy_[a];
+      }
+      const TA cm = wq * mu, cg = wq * q.gm, ch = wq * q.hb;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+#pragma unroll
+        for (int c = r; c < 8; ++c) {
+          const int a = r >> 1, ii = r & 1, b = c >> 1, kk = c & 1;
+          const TA va_i = ii ? vy[a] : vx[a], va_k = kk ? vy[a] : vx[a];
+          const TA vb_i = ii ? vy[b] : vx[b], vb_k = kk ? vy[b] : vx[b];
+          TA val = cg * va_i * vb_k - ch * vb_i * va_k;
+          if (ii == kk) val += cm * (gx_[a] * gx_[b] + gy_[a] * gy_[b]);
+          Ke[tri8(r, c)] += val;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 36; ++k) stage_k[(size_t)k * NN + slot] = Ke[k];
+}
+
+// Gather the 9-point stencil row of node (i,j) from the staged element tangents of the
+// four elements around it; optionally also L = dR/dFbar (rows of K times the affine field).
+template <typename TA>
+__device__ __forceinline__ void gather_stencil(int node, int n, const TA* stage_k, TA (&K)[9][4], bool withL,
+                                               TA (&L)[2][4]) {
+  const int NN = n * n, i = node % n, j = node / n;
+  const TA h = TA(1) / (TA)n;
+#pragma unroll
+  for (int nb = 0; nb < 9; ++nb)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) K[nb][c] = TA(0);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) L[a][c] = TA(0);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int ei = (i - offx(l) + n) % n, ej = (j - offy(l) + n) % n;
+    const int slot = ei + n * ej;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int nb = (offy(m) - offy(l) + 1) * 3 + (offx(m) - offx(l) + 1);
+#pragma unroll
+      for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const TA v = stage_k[(size_t)tri8(2 * l + ii, 2 * m + kk) * NN + slot];
+          K[nb][2 * ii + kk] += v;
+          if (withL) {
+            if (offx(m)) L[ii][2 * kk + 0] += v * h;
+            if (offy(m)) L[ii][2 * kk + 1] += v * h;
+          }
+        }
+    }
+  }
+}
+
+// y = K p for the owned node pair; p of neighbours from shared memory.
+template <typename TA, bool REG>
+__device__ __forceinline__ void apply_pair(const Stencil<TA, REG>& S, const Own2D& o, const vec2_t<TA>* ps,
+                                           const TA (&pown)[4], TA (&y)[4]) {
+  vec2_t<TA> P[4][3];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c == 1 && (r == 1 || r == 2)) continue;
+      P[r][c] = ps[o.rows[r] * o.n + o.cols[c]];
+    }
+  P[1][1] = mk2<TA>(pown[0], pown[1]);
+  P[2][1] = mk2<TA>(pown[2], pown[3]);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    TA yx = TA(0), yy = TA(0);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int nb = (dy + 1) * 3 + (dx + 1);
+        const vec2_t<TA> pv = P[1 + s + dy][1 + dx];
+        yx += S.get(s, nb, 0, o.node[s]) * pv.x + S.get(s, nb, 1, o.node[s]) * pv.y;
+        yy += S.get(s, nb, 2, o.node[s]) * pv.x + S.get(s, nb, 3, o.node[s]) * pv.y;
+      }
+    y[2 * s] = yx;
+    y[2 * s + 1] = yy;
+  }
+}
+
+// Block-Jacobi PCG for K x = b on the pinned periodic space.  All threads call it.
+// Returns the iteration count; *status receives kStatusPcgBreakdown / kStatusPcgCap.
+// truncate: for Newton corrections away from equilibrium the tangent may be indefinite; on
+// negative curvature the iteration stops with the step built so far (Steihaug's truncated
+// CG; on the first iteration the preconditioned residual direction with |p^T K p| as
+// curvature) and reports kStatusNegCurv, which the Newton loop accepts.
+template <typename TA, bool REG>
+__device__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& o, const TA (&Minv)[2][4], const TA (&b)[4],
+                        TA (&x)[4], TA rtol, int max_it, vec2_t<TA>* ps, TA* red0, TA* red1, int* status,
+                        bool truncate) {
+  TA r[4], z[4], p[4], Ap[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    x[k] = TA(0);
+    r[k] = o.active ? b[k] : TA(0);
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    z[2 * s] = Minv[s][0] * r[2 * s] + Minv[s][1] * r[2 * s + 1];
+    z[2 * s + 1] = Minv[s][2] * r[2 * s] + Minv[s][3] * r[2 * s + 1];
+  }
+  TA rz1[1] = {r[0] * z[0] + r[1] * z[1] + r[2] * z[2] + r[3] * z[3]};
+  block_sum<1, TA>(rz1, red1);
+  TA rz = rz1[0];
+  const TA rz0 = rz;
+  *status = kStatusOk;
+  if (!(rz0 > TA(0))) return 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) p[k] = z[k];
+  const TA stop = rtol * rtol * rz0;
+  int it = 0;
+  for (;;) {
+    if (it >= max_it) {
+      *status = kStatusPcgCap;
+      break;
+    }
+    if (o.active) {
+      ps[o.node[0]] = mk2<TA>(p[0], p[1]);
+      ps[o.node[1]] = mk2<TA>(p[2], p[3]);
+    }
+    __syncthreads();
+    if (o.active) {
+      apply_pair<TA, REG>(S, o, ps, p, Ap);
+      if (o.node[0] == 0) Ap[0] = Ap[1] = TA(0);  // pinned node
+    } else {
+      Ap[0] = Ap[1] = Ap[2] = Ap[3] = TA(0);
+    }
+    TA pap[1] = {p[0] * Ap[0] + p[1] * Ap[1] + p[2] * Ap[2] + p[3] * Ap[3]};
+    block_sum<1, TA>(pap, red0);
+    if (!(pap[0] > TA(0))) {
+      if (truncate && pap[0] < TA(0)) {
+        if (it == 0) {
+          const TA alpha0 = rz / -pap[0];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) x[k] = alpha0 * p[k];
+        }
+        *status = kStatusNegCurv;
+      } else {
+        *status = kStatusPcgBreakdown;
+      }
+      break;
+    }
+    const TA alpha = rz / pap[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      x[k] += alpha * p[k];
+      r[k] -= alpha * Ap[k];
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      z[2 * s] = Minv[s][0] * r[2 * s] + Minv[s][1] * r[2 * s + 1];
+      z[2 * s + 1] = Minv[s][2] * r[2 * s] + Minv[s][3] * r[2 * s + 1];
+    }
+    TA rzn[1] = {r[0] * z[0] + r[1] * z[1] + r[2] * z[2] + r[3] * z[3]};
+    block_sum<1, TA>(rzn, red1);
+    ++it;
+    if (rzn[0] <= stop) break;
+    const TA beta = rzn[0] / rz;
+    rz = rzn[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[k] = z[k] + beta * p[k];
+  }
+  return it;
+}
+
+template <typename TA>
+__device__ __forceinline__ void invert_block(const TA (&Kself)[4], bool pinned, TA (&Mi)[4]) {
+  const TA det = Kself[0] * Kself[3] - Kself[1] * Kself[2];
+  const TA id = pinned ? TA(0) : TA(1) / det;
+  Mi[0] = Kself[3] * id;
+  Mi[1] = -Kself[1] * id;
+  Mi[2] = -Kself[2] * id;
+  Mi[3] = Kself[0] * id;
+}
+
+// Assemble the tangent at the current w: element tangents -> stage, stencil gather, Minv.
+template <typename TA, bool REG>
+__device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& sm, TA* stage_k,
+                                              const TA (&Fb)[4], const uint8_t* phase, Stencil<TA, REG>& S,
+                                              TA (&Minv)[2][4], bool withL, TA (&L)[2][2][4]) {
+  const int n = o.n, NN = o.NN;
+  const vec2_t<TA>* wsrc;
+  if constexpr (REG) {
+    wsrc = reinterpret_cast<const vec2_t<TA>*>(sm.w32);
+  } else {
+    wsrc = reinterpret_cast<const vec2_t<TA>*>(sm.w);
+  }
+  if (o.active) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int e = o.node[s];
+      const int ph = phase[e];
+      element_tangent<TA>(e, n, wsrc, Fb, (TA)sm.lame[2 * ph], (TA)sm.lame[2 * ph + 1], stage_k, e, NN);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    TA Kn[9][4];
+    TA Ln[2][4];
+    if (o.active) {
+      gather_stencil<TA>(o.node[s], n, stage_k, Kn, withL, Ln);
+    } else {
+#pragma unroll
+      for (int nb = 0; nb < 9; ++nb)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Kn[nb][c] = TA(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Ln[a][c] = TA(0);
+    }
+    if constexpr (REG) {
+#pragma unroll
+      for (int nb = 0; nb < 9; ++nb)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) S.K[s][nb][c] = Kn[nb][c];
+    } else {
+      if (o.active) {
+#pragma unroll
+        for (int nb = 0; nb < 9; ++nb)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) S.g[(size_t)(nb * 4 + c) * NN + o.node[s]] = Kn[nb][c];
+      }
+    }
+    TA self[4] = {Kn[4][0], Kn[4][1], Kn[4][2], Kn[4][3]};
+    TA mi[4];
+    invert_block<TA>(self, !o.active || o.node[s] == 0, mi);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Minv[s][c] = mi[c];
+    if (withL) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) L[s][a][c] = Ln[a][c];
+    }
+  }
+  __syncthreads();  // stage reads done; global stencil writes visible
+}
+
+// Energy form of the tangent transfer over this thread's two elements (FP64 sums of
+// per-element TA partials).  X: [4][NN] periodic responses to the unit gradients.
+template <typename TA>
+__device__ __forceinline__ void element_transfer(int e, int n, const vec2_t<TA>* wsrc, const vec2_t<TA>* X,
+                                                 const TA (&Fb)[4], TA lam, TA mu, double (&Q)[10]) {
+  const int NN = n * n;
+  const int i = e % n, j = e / n, ip = (i + 1) % n, jp = (j + 1) % n;
+  const int nd[4] = {e, ip + n * j, ip + n * jp, i + n * jp};
+  const TA ih = (TA)n;
+  const vec2_t<TA> w0 = wsrc[nd[0]], w1 = wsrc[nd[1]], w2 = wsrc[nd[2]], w3 = wsrc[nd[3]];
+  vec2_t<TA> x[4][4];  // [rhs][local node]
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) x[c][a] = X[c * NN + nd[a]];
+  TA q[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) q[k] = TA(0);
+  const TA wq = TA(0.25) / (ih * ih);
+#pragma unroll
+  for (int gy = 0; gy < 2; ++gy) {
+    const TA t = (TA)gauss01(gy);
+#pragma unroll
+    for (int gx = 0; gx < 2; ++gx) {
+      const TA s = (TA)gauss01(gx);
+      const TA F00 = Fb[0] + ih * ((1 - t) * (w1.x - w0.x) + t * (w2.x - w3.x));
+      const TA F10 = Fb[2] + ih * ((1 - t) * (w1.y - w0.y) + t * (w2.y - w3.y));
+      const TA F01 = Fb[1] + ih * ((1 - s) * (w3.x - w0.x) + s * (w2.x - w1.x));
+      const TA F11 = Fb[3] + ih * ((1 - s) * (w3.y - w0.y) + s * (w2.y - w1.y));
+      const NH2<TA> nh = nh2_eval(F00, F01, F10, F11, lam, mu);
+      TA G[4][4];  // G_c = E_c + Grad X_c, row-major 2x2
+      TA M[4][4];  // M_c = Fit^T G_c
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const vec2_t<TA> a0 = x[c][0], a1 = x[c][1], a2 = x[c][2], a3 = x[c][3];
+        G[c][0] = ih * ((1 - t) * (a1.x - a0.x) + t * (a2.x - a3.x));
+        G[c][2] = ih * ((1 - t) * (a1.y - a0.y) + t * (a2.y - a3.y));
+        G[c][1] = ih * ((1 - s) * (a3.x - a0.x) + s * (a2.x - a1.x));
+        G[c][3] = ih * ((1 - s) * (a3.y - a0.y) + s * (a2.y - a1.y));
+        G[c][c] += TA(1);
+        // M_LJ = sum_i Fit_iL G_iJ
+        M[c][0] = nh.f00 * G[c][0] + nh.f10 * G[c][2];
+        M[c][1] = nh.f00 * G[c][1] + nh.f10 * G[c][3];
+        M[c][2] = nh.f01 * G[c][0] + nh.f11 * G[c][2];
+        M[c][3] = nh.f01 * G[c][1] + nh.f11 * G[c][3];
+      }
+      int k = 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int d = c; d < 4; ++d) {
+          const TA gg = G[c][0] * G[d][0] + G[c][1] * G[d][1] + G[c][2] * G[d][2] + G[c][3] * G[d][3];
+          // tr(M_c M_d)
+          const TA tm = M[c][0] * M[d][0] + M[c][1] * M[d][2] + M[c][2] * M[d][1] + M[c][3] * M[d][3];
+          const TA ac = M[c][0] + M[c][3], ad = M[d][0] + M[d][3];
+          q[k++] += wq * (mu * gg - nh.hb * tm + nh.gm * ac * ad);
+        }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k) Q[k] += (double)q[k];
+}
+
+template <typename TA>
+__device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, TA* gscr) {
+  constexpr bool REG = std::is_same<TA, float>::value;
+  const int tid = threadIdx.x;
+  const int rv = a.qp_rve[qp];
+  const int n = a.rve_n[rv];
+  const int NN = n * n;
+  const Own2D o = make_own(n);
+  const uint8_t* phase = a.phase + a.rve_phase_off[rv];
+  const double* w_in = a.w_in + a.qp_w_off[qp];
+  double* w_out = a.w_out + a.qp_w_off[qp];
+  double Fbd[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Fbd[k] = a.F[(size_t)qp * 4 + k];
+  TA Fb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Fb[k] = (TA)Fbd[k];
+  if (tid < 2 * kMaxPhase) sm.lame[tid] = a.rve_lame[(size_t)rv * 2 * kMaxPhase + tid];
+  for (int v = tid; v < NN; v += blockDim.x) {
+    double2 wv = make_double2(w_in[2 * v], w_in[2 * v + 1]);
+    if (v == 0) wv = make_double2(0.0, 0.0);
+    sm.w[v] = wv;
+    if constexpr (REG) sm.w32[v] = make_float2((float)wv.x, (float)wv.y);
+  }
+  __syncthreads();
+
+  double* stage_f = reinterpret_cast<double*>(sm.stage);
+  TA* stage_k = REG ? reinterpret_cast<TA*>(sm.stage) : gscr + (size_t)36 * NN;
+  Stencil<TA, REG> S;
+  S.g = gscr;
+  S.NN = NN;
+  TA* redA = reinterpret_cast<TA*>(sm.red);
+  TA* redB = reinterpret_cast<TA*>(sm.red + 512);
+  TA Minv[2][4];
+  TA Ldummy[2][2][4];
+
+  int status = kStatusNewtonCap, it = 0, cg_total = 0;
+  double r0 = 0.0;
+  double Psum[4];
+  for (;;) {
+    // ---- FP64 residual
+    Psum[0] = Psum[1] = Psum[2] = Psum[3] = 0.0;
+    double bad = 0.0;
+    if (o.active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int e = o.node[s];
+        const int ph = phase[e];
+        element_residual(e, n, sm.w, Fbd, sm.lame[2 * ph], sm.lame[2 * ph + 1], stage_f, Psum, bad);
+      }
+    }
+    __syncthreads();
+    double R[4] = {0, 0, 0, 0};
+    if (o.active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int nd = o.node[s], i = nd % n, j = nd / n;
+        const int im = (i - 1 + n) % n, jm = (j - 1 + n) % n;
+        const int eA = nd, eB = im + n * j, eC = im + n * jm, eD = i + n * jm;
+        R[2 * s] = stage_f[0 * NN + eA] + stage_f[2 * NN + eB] + stage_f[4 * NN + eC] + stage_f[6 * NN + eD];
+        R[2 * s + 1] = stage_f[1 * NN + eA] + stage_f[3 * NN + eB] + stage_f[5 * NN + eC] + stage_f[7 * NN + eD];
+      }
+      if (o.node[0] == 0) R[0] = R[1] = 0.0;
+    }
+    double v2[2] = {R[0] * R[0] + R[1] * R[1] + R[2] * R[2] + R[3] * R[3], bad};
+    block_sum<2, double>(v2, sm.red + (it & 1) * 512);
+    const double rn = sqrt(v2[0]);
+    if (it == 0) r0 = rn;
+    if (v2[1] > 0.0) {
+      status = kStatusJNonPos;
+      break;
+    }
+    if (!isfinite(rn)) {
+      status = kStatusNonFinite;
+      break;
+    }
+    if (rn <= fmax(a.newton_rtol * r0, a.newton_atol)) {
+      status = kStatusOk;
+      break;
+    }
+    if (it >= a.max_newton) {
+      status = kStatusNewtonCap;
+      break;
+    }
+    // ---- tangent and PCG correction
+    build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, false, Ldummy);
+    TA b[4], x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b[k] = (TA)(-R[k]);
+    int pst = kStatusOk;
+    cg_total += pcg_pair<TA, REG>(S, o, Minv, b, x, (TA)a.cg_rtol, a.max_cg, sm.p, redA, redB, &pst, true);
+    if (pst == kStatusPcgBreakdown) {
+      status = kStatusPcgBreakdown;
+      break;
+    }
+    if (o.active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int nd = o.node[s];
+        double2 wv = sm.w[nd];
+        wv.x += (double)x[2 * s];
+        wv.y += (double)x[2 * s + 1];
+        sm.w[nd] = wv;
+        if constexpr (REG) sm.w32[nd] = make_float2((float)wv.x, (float)wv.y);
+      }
+    }
+    __syncthreads();
+    ++it;
+  }
+
+  // ---- homogenised stress (and energy) at the final state
+  double Pv[5] = {Psum[0], Psum[1], Psum[2], Psum[3], 0.0};
+  const bool usable = (status == kStatusOk || status == kStatusNewtonCap);
+  const bool want_W = usable && (a.flags & kFlagEnergy) && a.W != nullptr;
+  if (want_W && o.active) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int e = o.node[s];
+      const int ph = phase[e];
+      Pv[4] += element_energy(e, n, sm.w, Fbd, sm.lame[2 * ph], sm.lame[2 * ph + 1]);
+    }
+  }
+  // the last residual norm used buffer (it & 1) and may still be read: use the other one
+  block_sum<5, double>(Pv, sm.red + ((it + 1) & 1) * 512);
+  const double wq = 0.25 / ((double)n * n);  // |Omega| = 1
+
+  // ---- tangent transfer (condensation) at the converged state
+  int cond_total = 0, cond_max = 0;
+  double Q[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) Q[k] = 0.0;
+  const bool want_A = usable && !(a.flags & kFlagNoTangent) && a.A != nullptr;
+  if (want_A) {
+    TA L[2][2][4];
+    build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, true, L);
+    vec2_t<TA>* X = reinterpret_cast<vec2_t<TA>*>(sm.stage);
+    for (int c = 0; c < 4; ++c) {
+      TA b[4], x[4];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        b[2 * s] = -L[s][0][c];
+        b[2 * s + 1] = -L[s][1][c];
+      }
+      if (o.node[0] == 0) b[0] = b[1] = TA(0);
+      int pst = kStatusOk;
+      const int ci = pcg_pair<TA, REG>(S, o, Minv, b, x, (TA)a.cond_rtol, a.max_cond_cg, sm.p, redA, redB, &pst,
+                                        false);
+      cond_total += ci;
+      cond_max = ci > cond_max ? ci : cond_max;
+      if (pst != kStatusOk && status == kStatusOk) status = pst;
+      if (o.active) {
+        X[c * NN + o.node[0]] = mk2<TA>(x[0], x[1]);
+        X[c * NN + o.node[1]] = mk2<TA>(x[2], x[3]);
+      }
+    }
+    __syncthreads();
+    const vec2_t<TA>* wsrc;
+    if constexpr (REG) {
+      wsrc = reinterpret_cast<const vec2_t<TA>*>(sm.w32);
+    } else {
+      wsrc = reinterpret_cast<const vec2_t<TA>*>(sm.w);
+    }
+    if (o.active) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int e = o.node[s];
+        const int ph = phase[e];
+        element_transfer<TA>(e, n, wsrc, X, Fb, (TA)sm.lame[2 * ph], (TA)sm.lame[2 * ph + 1], Q);
+      }
+    }
+    block_sum<10, double>(Q, sm.red + (it & 1) * 512);
+  }
+
+  // ---- outputs
+  for (int v = tid; v < NN; v += blockDim.x) {
+    const double2 wv = sm.w[v];
+    w_out[2 * v] = wv.x;
+    w_out[2 * v + 1] = wv.y;
+  }
+  if (tid == 0) {
+    a.status[qp] = status;
+    if (a.iters) {
+      a.iters[(size_t)qp * 4 + 0] = it;
+      a.iters[(size_t)qp * 4 + 1] = cg_total;
+      a.iters[(size_t)qp * 4 + 2] = cond_total;
+      a.iters[(size_t)qp * 4 + 3] = cond_max;
+    }
+    if (usable) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a.P[(size_t)qp * 4 + k] = Pv[k] * wq;
+      if (want_W) a.W[qp] = Pv[4] * wq;
+      if (want_A) {
+        int k = 0;
+        for (int c = 0; c < 4; ++c)
+          for (int d = c; d < 4; ++d) {
+            a.A[(size_t)qp * 16 + c * 4 + d] = Q[k];
+            a.A[(size_t)qp * 16 + d * 4 + c] = Q[k];
+            ++k;
+          }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(kThreads2D, 1) rve2d_kernel(const Rve2dArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem2D<TA> sm;
+  smem2d_layout<TA>(a.nn_max, &sm, smem_raw);
+  __shared__ int s_item;
+  constexpr bool REG = std::is_same<TA, float>::value;
+  TA* gscr = REG ? nullptr : reinterpret_cast<TA*>(a.scratch) + (size_t)blockIdx.x * 72 * a.nn_max;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= a.n_qp) break;
+    solve_item_2d<TA>(a, a.order[item], sm, gscr);
+  }
+}
+
+}  // namespace
+
+size_t rve2d_smem_bytes(int nn_max, bool mixed) {
+  return mixed ? smem2d_layout<float>(nn_max, nullptr, nullptr) : smem2d_layout<double>(nn_max, nullptr, nullptr);
+}
+
+size_t rve2d_scratch_bytes(int nn_max, bool mixed, int n_blocks) {
+  return mixed ? 0 : sizeof(double) * 72 * (size_t)nn_max * n_blocks;
+}
+
+int rve2d_threads() { return kThreads2D; }
+
+cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream) {
+  const size_t smem = rve2d_smem_bytes(a.nn_max, mixed);
+  cudaError_t err;
+  if (mixed) {
+    err = cudaFuncSetAttribute(rve2d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    rve2d_kernel<float><<<n_blocks, kThreads2D, smem, stream>>>(a);
+  } else {
+    err = cudaFuncSetAttribute(rve2d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    rve2d_kernel<double><<<n_blocks, kThreads2D, smem, stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fehmm

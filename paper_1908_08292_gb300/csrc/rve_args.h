@@ -1,0 +1,56 @@
+// Launch arguments of the batched RVE kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace fehmm {
+
+struct Rve2dArgs {
+  int n_qp;                     // quadrature points in the batch
+  int nn_max;                   // largest n^2 over the batch (sizes shared memory)
+  const int32_t* order;         // [n_qp] processing order (largest RVE first)
+  const int32_t* qp_rve;        // [n_qp] microstructure of each point
+  const int32_t* rve_n;         // [n_rve] grid size
+  const int64_t* rve_phase_off; // [n_rve] offset of the phase map
+  const uint8_t* phase;         // concatenated phase maps
+  const double* rve_lame;       // [n_rve][kMaxPhase][2] (lambda, mu)
+  const int64_t* qp_w_off;      // [n_qp] offset (doubles) of each fluctuation field
+  const double* w_in;           // start fluctuations
+  double* w_out;                // result fluctuations (may alias w_in)
+  const double* F;             // [n_qp][4]
+  double* P;                    // [n_qp][4]
+  double* A;                    // [n_qp][16] or null
+  double* W;                    // [n_qp] or null
+  int32_t* status;              // [n_qp]
+  int32_t* iters;               // [n_qp][4] or null
+  int32_t* queue;               // work counter, zero at launch
+  void* scratch;                // per-block global scratch (FP64 mode)
+  double newton_rtol, newton_atol, cg_rtol, cond_rtol;
+  int max_newton, max_cg, max_cond_cg, flags;
+};
+
+size_t rve2d_smem_bytes(int nn_max, bool mixed);
+size_t rve2d_scratch_bytes(int nn_max, bool mixed, int n_blocks);
+int rve2d_threads();
+cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream);
+
+struct MacroArgs {
+  int dim;
+  int nel[3];           // elements per axis
+  int n_el, n_nodes, n_qp, nq, nen;
+  double h[3];
+  const double* u;      // [n_nodes*dim]
+  double* F;            // [n_qp][d*d]
+  const double* P;      // [n_qp][d*d]
+  const double* A;      // [n_qp][d^4]
+  double* f;            // [n_nodes*dim]
+  double* K;            // [nnz]
+  const int32_t* blk_base;    // [n_el][nen][nen] CSR position of the (I,J) block's (0,0) entry
+  const int32_t* blk_stride;  // [n_el][nen] row stride (entries) between the dim rows of node I
+};
+
+cudaError_t macro_qp_F_launch(const MacroArgs& m, cudaStream_t stream);
+cudaError_t macro_assemble_launch(const MacroArgs& m, cudaStream_t stream, int* launches);
+
+}  // namespace fehmm
