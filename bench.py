@@ -148,7 +148,8 @@ def run_gpu(args):
     fe.lib()
     p, Fload = build_problem(args.step_index)
     n_qp = p.n_qp
-    ctx = fe.Context(2, "mixed")
+    opts = {k: v for k, v in (("cg_rtol", args.cg_rtol), ("cond_rtol", args.cond_rtol)) if v is not None}
+    ctx = fe.Context(2, "mixed", **opts)
     ctx.add_rves(p.rve_n, p.rve_phase, p.rve_E, p.rve_nu)
     ctx.bind_qps(p.qp_rve)
     ctx.macro_create([_SIZE["macro"]] * 2)
@@ -323,6 +324,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rves-per-step", type=int, default=4)
+    ap.add_argument("--cg-rtol", type=float, default=None, help="override the Newton-correction PCG tolerance")
+    ap.add_argument("--cond-rtol", type=float, default=None, help="override the tangent-transfer PCG tolerance")
     ap.add_argument("--macro", type=int, default=MACRO, help="macro elements per axis (profiling runs use less)")
     args = ap.parse_args()
     _SIZE["macro"] = args.macro

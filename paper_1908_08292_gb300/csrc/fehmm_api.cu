@@ -90,7 +90,7 @@ int fehmm_default_options(fehmm_options* opt, int dim, int precision) {
   opt->max_newton = 25;
   opt->cg_rtol = precision == FEHMM_PREC_FP64 ? 1e-6 : 1e-4;
   opt->max_cg = 2000;
-  opt->cond_rtol = precision == FEHMM_PREC_FP64 ? 1e-9 : 1e-5;
+  opt->cond_rtol = precision == FEHMM_PREC_FP64 ? 1e-9 : 1e-6;
   opt->max_cond_cg = 4000;
   return FEHMM_OK;
 }

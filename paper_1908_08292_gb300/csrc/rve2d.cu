@@ -54,10 +54,12 @@ template <typename TA>
 struct Smem2D {
   double2* w;        // [NN] fluctuation (FP64)
   float2* w32;       // [NN] FP32 copy (mixed mode only)
-  vec2_t<TA>* p;     // [NN] PCG search direction
+  vec2_t<TA>* p;     // [NN] PCG exchange vector (u = M^-1 r)
+  vec2_t<TA>* x;     // [NN] PCG solution (owned nodes written by their thread)
   unsigned char* stage;  // element forces / element tangents / condensation solutions
   double* red;       // 2 x 512 doubles of reduction buffers
   double* lame;      // [kMaxPhase][2]
+  double* misc;      // [16]: Fbar (0..3), homogenised P and W (4..8)
 };
 
 template <typename TA>
@@ -72,19 +74,24 @@ __host__ __device__ inline size_t smem2d_layout(int NN, Smem2D<TA>* s, unsigned 
   size_t o_w = take(sizeof(double2) * NN);
   size_t o_w32 = REG ? take(sizeof(float2) * NN) : 0;
   size_t o_p = take(sizeof(vec2_t<TA>) * NN);
+  size_t o_x = take(sizeof(vec2_t<TA>) * NN);
   size_t stage_bytes = sizeof(double) * 8 * NN;                               // element forces
   if (REG && sizeof(float) * 36 * NN > stage_bytes) stage_bytes = sizeof(float) * 36 * NN;  // Ke
-  if (sizeof(vec2_t<TA>) * 4 * NN > stage_bytes) stage_bytes = sizeof(vec2_t<TA>) * 4 * NN;  // X
+  // condensation solutions X[4][NN] and right-hand sides L[4][NN]
+  if (sizeof(vec2_t<TA>) * 8 * NN > stage_bytes) stage_bytes = sizeof(vec2_t<TA>) * 8 * NN;
   size_t o_stage = take(stage_bytes);
   size_t o_red = take(sizeof(double) * 2 * 512);
   size_t o_lame = take(sizeof(double) * 2 * kMaxPhase);
+  size_t o_misc = take(sizeof(double) * 16);
   if (s) {
     s->w = reinterpret_cast<double2*>(base + o_w);
     s->w32 = REG ? reinterpret_cast<float2*>(base + o_w32) : nullptr;
     s->p = reinterpret_cast<vec2_t<TA>*>(base + o_p);
+    s->x = reinterpret_cast<vec2_t<TA>*>(base + o_x);
     s->stage = base + o_stage;
     s->red = reinterpret_cast<double*>(base + o_red);
     s->lame = reinterpret_cast<double*>(base + o_lame);
+    s->misc = reinterpret_cast<double*>(base + o_misc);
   }
   return off;
 }
@@ -94,7 +101,7 @@ struct Own2D {
   int n, NN, col, strip;
   bool active;
   int node[2];   // (col, 2*strip), (col, 2*strip+1)
-  int rows[4];   // 2s-1, 2s, 2s+1, 2s+2 (periodic)
+  int rows[4];   // (2s-1, 2s, 2s+1, 2s+2 periodic) * n: row offsets
   int cols[3];   // col-1, col, col+1 (periodic)
 };
 
@@ -106,32 +113,29 @@ __device__ __forceinline__ Own2D make_own(int n) {
   o.col = t % n;
   o.strip = t / n;
   o.active = o.strip < n / 2;
+  if (!o.active) o.col = o.strip = 0;  // idle threads: every derived index stays inside the RVE
   const int r0 = 2 * o.strip;
   o.node[0] = o.col + n * r0;
   o.node[1] = o.node[0] + n;
-  o.rows[0] = (r0 - 1 + n) % n;
-  o.rows[1] = r0;
-  o.rows[2] = (r0 + 1) % n;
-  o.rows[3] = (r0 + 2) % n;
+  o.rows[0] = ((r0 - 1 + n) % n) * n;
+  o.rows[1] = r0 * n;
+  o.rows[2] = ((r0 + 1) % n) * n;
+  o.rows[3] = ((r0 + 2) % n) * n;
   o.cols[0] = (o.col - 1 + n) % n;
   o.cols[1] = o.col;
   o.cols[2] = (o.col + 1) % n;
   return o;
 }
 
-// Stencil storage: REG -> K[2][9][4] registers; else global scratch [36][NN].
+// Stencil storage.  REG (FP32): registers, block nb of owned node s as two row pairs
+// K2[s][nb][0] = (K_xx, K_xy), K2[s][nb][1] = (K_yx, K_yy), consumed by paired FP32 FMAs
+// (FFMA2).  Otherwise (FP64): global scratch [36][NN] in row-major block order.
 template <typename TA, bool REG>
 struct Stencil {
-  TA K[2][9][4];
+  float2 K2[2][9][2];
   TA* g;  // global stencil base (FP64 mode)
   int NN;
-  __device__ __forceinline__ TA get(int s, int nb, int c, int node) const {
-    if constexpr (REG) {
-      return K[s][nb][c];
-    } else {
-      return g[(size_t)(nb * 4 + c) * NN + node];
-    }
-  }
+  __device__ __forceinline__ TA get(int nb, int c, int node) const { return g[(size_t)(nb * 4 + c) * NN + node]; }
 };
 
 // ------------------------------------------------------------------ residual (FP64)
@@ -305,118 +309,232 @@ __device__ __forceinline__ void gather_stencil(int node, int n, const TA* stage_
   }
 }
 
-// y = K p for the owned node pair; p of neighbours from shared memory.
+// y = K p for the owned node pair; p of neighbours from shared memory.  The four
+// neighbour rows (2s-1 .. 2s+2) are streamed one at a time: row r feeds the lower node
+// (row offset r-1) and the upper node (row offset r-2), so only one row is live.
 template <typename TA, bool REG>
 __device__ __forceinline__ void apply_pair(const Stencil<TA, REG>& S, const Own2D& o, const vec2_t<TA>* ps,
                                            const TA (&pown)[4], TA (&y)[4]) {
-  vec2_t<TA> P[4][3];
+  if constexpr (REG) {
+    // acc[s][i] accumulates (K_i0 p_x, K_i1 p_y) pairs; y_i = acc.x + acc.y at the end
+    float2 acc[2][2] = {{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}};
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 4; ++r) {
+      float2 P[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (c == 1 && (r == 1 || r == 2)) continue;
-      P[r][c] = ps[o.rows[r] * o.n + o.cols[c]];
-    }
-  P[1][1] = mk2<TA>(pown[0], pown[1]);
-  P[2][1] = mk2<TA>(pown[2], pown[3]);
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    TA yx = TA(0), yy = TA(0);
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int nb = (dy + 1) * 3 + (dx + 1);
-        const vec2_t<TA> pv = P[1 + s + dy][1 + dx];
-        yx += S.get(s, nb, 0, o.node[s]) * pv.x + S.get(s, nb, 1, o.node[s]) * pv.y;
-        yy += S.get(s, nb, 2, o.node[s]) * pv.x + S.get(s, nb, 3, o.node[s]) * pv.y;
+      for (int c = 0; c < 3; ++c) {
+        if (c == 1 && r == 1) {
+          P[c] = make_float2(pown[0], pown[1]);
+        } else if (c == 1 && r == 2) {
+          P[c] = make_float2(pown[2], pown[3]);
+        } else {
+          P[c] = ps[o.rows[r] + o.cols[c]];
+        }
       }
-    y[2 * s] = yx;
-    y[2 * s + 1] = yy;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (r <= 2) {
+          const int nb = r * 3 + c;
+          acc[0][0] = __ffma2_rn(S.K2[0][nb][0], P[c], acc[0][0]);
+          acc[0][1] = __ffma2_rn(S.K2[0][nb][1], P[c], acc[0][1]);
+        }
+        if (r >= 1) {
+          const int nb = (r - 1) * 3 + c;
+          acc[1][0] = __ffma2_rn(S.K2[1][nb][0], P[c], acc[1][0]);
+          acc[1][1] = __ffma2_rn(S.K2[1][nb][1], P[c], acc[1][1]);
+        }
+      }
+    }
+    y[0] = acc[0][0].x + acc[0][0].y;
+    y[1] = acc[0][1].x + acc[0][1].y;
+    y[2] = acc[1][0].x + acc[1][0].y;
+    y[3] = acc[1][1].x + acc[1][1].y;
+  } else {
+    TA y0x = TA(0), y0y = TA(0), y1x = TA(0), y1y = TA(0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      vec2_t<TA> P[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (c == 1 && r == 1) {
+          P[c] = mk2<TA>(pown[0], pown[1]);
+        } else if (c == 1 && r == 2) {
+          P[c] = mk2<TA>(pown[2], pown[3]);
+        } else {
+          P[c] = ps[o.rows[r] + o.cols[c]];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (r <= 2) {
+          const int nb = r * 3 + c;
+          y0x += S.get(nb, 0, o.node[0]) * P[c].x + S.get(nb, 1, o.node[0]) * P[c].y;
+          y0y += S.get(nb, 2, o.node[0]) * P[c].x + S.get(nb, 3, o.node[0]) * P[c].y;
+        }
+        if (r >= 1) {
+          const int nb = (r - 1) * 3 + c;
+          y1x += S.get(nb, 0, o.node[1]) * P[c].x + S.get(nb, 1, o.node[1]) * P[c].y;
+          y1y += S.get(nb, 2, o.node[1]) * P[c].x + S.get(nb, 3, o.node[1]) * P[c].y;
+        }
+      }
+    }
+    y[0] = y0x;
+    y[1] = y0y;
+    y[2] = y1x;
+    y[3] = y1y;
   }
 }
 
-// Block-Jacobi PCG for K x = b on the pinned periodic space.  All threads call it.
-// Returns the iteration count; *status receives kStatusPcgBreakdown / kStatusPcgCap.
+// Quotient for the CG step scalars: fast reciprocal-based division in FP32 (a few ulp,
+// irrelevant for the step lengths), IEEE division in FP64 mode.
+template <typename T>
+__device__ __forceinline__ T cg_div(T a, T b) {
+  if constexpr (sizeof(T) == 4) {
+    return __fdividef(a, b);
+  } else {
+    return a / b;
+  }
+}
+
+// Sum of two per-thread values over the block (every thread receives both totals): warp
+// shuffles, one barrier, then a broadcast read of the 16 warp partials from shared memory.
+// buf holds 2*16 values; callers alternate buffers between consecutive calls.
+template <typename T>
+__device__ __forceinline__ void block_sum2(T& a, T& b, T* buf) {
+  static_assert(kThreads2D == 512, "16 warps assumed");
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    buf[2 * warp] = a;
+    buf[2 * warp + 1] = b;
+  }
+  __syncthreads();
+  T sa[4] = {T(0), T(0), T(0), T(0)}, sb[4] = {T(0), T(0), T(0), T(0)};
+  if constexpr (sizeof(T) == 4) {
+    const float4* b4 = reinterpret_cast<const float4*>(buf);  // (a_w, b_w, a_w+1, b_w+1)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float4 v = b4[k];
+      sa[k & 3] += v.x + v.z;
+      sb[k & 3] += v.y + v.w;
+    }
+  } else {
+    const double2* b2 = reinterpret_cast<const double2*>(buf);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const double2 v = b2[k];
+      sa[k & 3] += v.x;
+      sb[k & 3] += v.y;
+    }
+  }
+  a = (sa[0] + sa[1]) + (sa[2] + sa[3]);
+  b = (sb[0] + sb[1]) + (sb[2] + sb[3]);
+}
+
+// Block-Jacobi preconditioned CG for K x = b on the pinned periodic space, in the
+// single-reduction form of Chronopoulos and Gear (one fused block reduction of
+// gamma = r.u and delta = u.Ku per iteration, u = M^-1 r; p and s = K p follow by
+// recurrence).  All threads call it.  x is accumulated in shared memory (xs, the owned
+// nodes only).  Returns the iteration count; *status receives kStatusPcgCap /
+// kStatusPcgBreakdown / kStatusNegCurv.
 // truncate: for Newton corrections away from equilibrium the tangent may be indefinite; on
-// negative curvature the iteration stops with the step built so far (Steihaug's truncated
-// CG; on the first iteration the preconditioned residual direction with |p^T K p| as
-// curvature) and reports kStatusNegCurv, which the Newton loop accepts.
+// negative curvature (p^T K p <= 0) the iteration stops with the step built so far
+// (Steihaug's truncated CG; on the first iteration the preconditioned residual direction with
+// |p^T K p| as curvature) and reports kStatusNegCurv, which the Newton loop accepts.
 template <typename TA, bool REG>
-__device__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& o, const TA (&Minv)[2][4], const TA (&b)[4],
-                        TA (&x)[4], TA rtol, int max_it, vec2_t<TA>* ps, TA* red0, TA* red1, int* status,
+__device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& o, const TA (&Minv)[2][4],
+                                        const TA (&b)[4],
+                        vec2_t<TA>* xs, TA rtol, int max_it, vec2_t<TA>* ps, TA* red0, TA* red1, int* status,
                         bool truncate) {
-  TA r[4], z[4], p[4], Ap[4];
+  TA r[4], u[4], w[4], p[4], s[4], x[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    x[k] = TA(0);
     r[k] = o.active ? b[k] : TA(0);
+    x[k] = TA(0);
   }
+  auto precond = [&]() {  // u = M^-1 r with the inverted nodal 2x2 blocks (zero on idle threads)
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    z[2 * s] = Minv[s][0] * r[2 * s] + Minv[s][1] * r[2 * s + 1];
-    z[2 * s + 1] = Minv[s][2] * r[2 * s] + Minv[s][3] * r[2 * s + 1];
-  }
-  TA rz1[1] = {r[0] * z[0] + r[1] * z[1] + r[2] * z[2] + r[3] * z[3]};
-  block_sum<1, TA>(rz1, red1);
-  TA rz = rz1[0];
-  const TA rz0 = rz;
-  *status = kStatusOk;
-  if (!(rz0 > TA(0))) return 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) p[k] = z[k];
-  const TA stop = rtol * rtol * rz0;
-  int it = 0;
-  for (;;) {
-    if (it >= max_it) {
-      *status = kStatusPcgCap;
-      break;
+    for (int q = 0; q < 2; ++q) {
+      u[2 * q] = Minv[q][0] * r[2 * q] + Minv[q][1] * r[2 * q + 1];
+      u[2 * q + 1] = Minv[q][2] * r[2 * q] + Minv[q][3] * r[2 * q + 1];
     }
+  };
+  auto exchange_apply = [&]() {  // w = K u
     if (o.active) {
-      ps[o.node[0]] = mk2<TA>(p[0], p[1]);
-      ps[o.node[1]] = mk2<TA>(p[2], p[3]);
+      ps[o.node[0]] = mk2<TA>(u[0], u[1]);
+      ps[o.node[1]] = mk2<TA>(u[2], u[3]);
     }
     __syncthreads();
     if (o.active) {
-      apply_pair<TA, REG>(S, o, ps, p, Ap);
-      if (o.node[0] == 0) Ap[0] = Ap[1] = TA(0);  // pinned node
+      apply_pair<TA, REG>(S, o, ps, u, w);
+      if (o.node[0] == 0) w[0] = w[1] = TA(0);  // pinned node
     } else {
-      Ap[0] = Ap[1] = Ap[2] = Ap[3] = TA(0);
+      w[0] = w[1] = w[2] = w[3] = TA(0);
     }
-    TA pap[1] = {p[0] * Ap[0] + p[1] * Ap[1] + p[2] * Ap[2] + p[3] * Ap[3]};
-    block_sum<1, TA>(pap, red0);
-    if (!(pap[0] > TA(0))) {
-      if (truncate && pap[0] < TA(0)) {
-        if (it == 0) {
-          const TA alpha0 = rz / -pap[0];
+  };
+  *status = kStatusOk;
+  precond();
+  exchange_apply();
+  TA gamma = r[0] * u[0] + r[1] * u[1] + r[2] * u[2] + r[3] * u[3];
+  TA delta = w[0] * u[0] + w[1] * u[1] + w[2] * u[2] + w[3] * u[3];
+  block_sum2<TA>(gamma, delta, red1);
+  const TA gamma0 = gamma;
+  int it = 0;
+  if (gamma0 > TA(0)) {
+    if (!(delta > TA(0))) {
+      if (truncate && delta < TA(0)) {
+        const TA a0 = cg_div<TA>(gamma, -delta);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) x[k] = alpha0 * p[k];
-        }
+        for (int k = 0; k < 4; ++k) x[k] = a0 * u[k];
         *status = kStatusNegCurv;
       } else {
         *status = kStatusPcgBreakdown;
       }
-      break;
-    }
-    const TA alpha = rz / pap[0];
+    } else {
+      const TA stop = rtol * rtol * gamma0;
+      TA alpha = cg_div<TA>(gamma, delta);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      x[k] += alpha * p[k];
-      r[k] -= alpha * Ap[k];
-    }
+      for (int k = 0; k < 4; ++k) {
+        p[k] = u[k];
+        s[k] = w[k];
+      }
+      for (;;) {
+        if (it >= max_it) {
+          *status = kStatusPcgCap;
+          break;
+        }
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      z[2 * s] = Minv[s][0] * r[2 * s] + Minv[s][1] * r[2 * s + 1];
-      z[2 * s + 1] = Minv[s][2] * r[2 * s] + Minv[s][3] * r[2 * s + 1];
-    }
-    TA rzn[1] = {r[0] * z[0] + r[1] * z[1] + r[2] * z[2] + r[3] * z[3]};
-    block_sum<1, TA>(rzn, red1);
-    ++it;
-    if (rzn[0] <= stop) break;
-    const TA beta = rzn[0] / rz;
-    rz = rzn[0];
+        for (int k = 0; k < 4; ++k) {
+          x[k] += alpha * p[k];
+          r[k] -= alpha * s[k];
+        }
+        precond();
+        exchange_apply();
+        TA gn = r[0] * u[0] + r[1] * u[1] + r[2] * u[2] + r[3] * u[3];
+        TA dn = w[0] * u[0] + w[1] * u[1] + w[2] * u[2] + w[3] * u[3];
+        block_sum2<TA>(gn, dn, (it & 1) ? red1 : red0);
+        ++it;
+        if (gn <= stop) break;
+        const TA beta = cg_div<TA>(gn, gamma);
+        const TA den = dn - beta * cg_div<TA>(gn, alpha);  // p_new^T K p_new
+        if (!(den > TA(0))) {
+          *status = (truncate && den < TA(0)) ? kStatusNegCurv : kStatusPcgBreakdown;
+          break;
+        }
+        alpha = cg_div<TA>(gn, den);
+        gamma = gn;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) p[k] = z[k] + beta * p[k];
+        for (int k = 0; k < 4; ++k) {
+          p[k] = u[k] + beta * p[k];
+          s[k] = w[k] + beta * s[k];
+        }
+      }
+    }
+  }
+  if (o.active) {
+    xs[o.node[0]] = mk2<TA>(x[0], x[1]);
+    xs[o.node[1]] = mk2<TA>(x[2], x[3]);
   }
   return it;
 }
@@ -432,10 +550,14 @@ __device__ __forceinline__ void invert_block(const TA (&Kself)[4], bool pinned, 
 }
 
 // Assemble the tangent at the current w: element tangents -> stage, stencil gather, Minv.
+// Minv (inverted nodal blocks, zero on idle threads and the pinned node) stays in
+// registers; with withL the condensation right-hand sides go to shared memory,
+// Lb[c][NN] = -L_c of each owned node.
 template <typename TA, bool REG>
 __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& sm, TA* stage_k,
                                               const TA (&Fb)[4], const uint8_t* phase, Stencil<TA, REG>& S,
-                                              TA (&Minv)[2][4], bool withL, TA (&L)[2][2][4]) {
+                                              TA (&Minv)[2][4], bool withL, vec2_t<TA>* Lb) {
+  TA L[2][2][4];
   const int n = o.n, NN = o.NN;
   const vec2_t<TA>* wsrc;
   if constexpr (REG) {
@@ -470,9 +592,10 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
     }
     if constexpr (REG) {
 #pragma unroll
-      for (int nb = 0; nb < 9; ++nb)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) S.K[s][nb][c] = Kn[nb][c];
+      for (int nb = 0; nb < 9; ++nb) {
+        S.K2[s][nb][0] = make_float2(Kn[nb][0], Kn[nb][1]);
+        S.K2[s][nb][1] = make_float2(Kn[nb][2], Kn[nb][3]);
+      }
     } else {
       if (o.active) {
 #pragma unroll
@@ -494,6 +617,18 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
     }
   }
   __syncthreads();  // stage reads done; global stencil writes visible
+  if (o.active && withL) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const bool pinned = o.node[s] == 0;
+          Lb[c * o.NN + o.node[s]] = mk2<TA>(pinned ? TA(0) : -L[s][0][c], pinned ? TA(0) : -L[s][1][c]);
+        }
+      }
+    }
+  }
 }
 
 // Energy form of the tangent transfer over this thread's two elements (FP64 sums of
@@ -577,6 +712,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
 #pragma unroll
   for (int k = 0; k < 4; ++k) Fb[k] = (TA)Fbd[k];
   if (tid < 2 * kMaxPhase) sm.lame[tid] = a.rve_lame[(size_t)rv * 2 * kMaxPhase + tid];
+  if (tid < 4) sm.misc[tid] = Fbd[tid];
   for (int v = tid; v < NN; v += blockDim.x) {
     double2 wv = make_double2(w_in[2 * v], w_in[2 * v + 1]);
     if (v == 0) wv = make_double2(0.0, 0.0);
@@ -592,8 +728,9 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   S.NN = NN;
   TA* redA = reinterpret_cast<TA*>(sm.red);
   TA* redB = reinterpret_cast<TA*>(sm.red + 512);
+  vec2_t<TA>* Xs = reinterpret_cast<vec2_t<TA>*>(sm.stage);  // [4][NN]
+  vec2_t<TA>* Lb = Xs + 4 * NN;                               // [4][NN]
   TA Minv[2][4];
-  TA Ldummy[2][2][4];
 
   int status = kStatusNewtonCap, it = 0, cg_total = 0;
   double r0 = 0.0;
@@ -644,12 +781,12 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       break;
     }
     // ---- tangent and PCG correction
-    build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, false, Ldummy);
-    TA b[4], x[4];
+    build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb);
+    TA b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) b[k] = (TA)(-R[k]);
     int pst = kStatusOk;
-    cg_total += pcg_pair<TA, REG>(S, o, Minv, b, x, (TA)a.cg_rtol, a.max_cg, sm.p, redA, redB, &pst, true);
+    cg_total += pcg_pair<TA, REG>(S, o, Minv, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redA, redB, &pst, true);
     if (pst == kStatusPcgBreakdown) {
       status = kStatusPcgBreakdown;
       break;
@@ -659,8 +796,9 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       for (int s = 0; s < 2; ++s) {
         const int nd = o.node[s];
         double2 wv = sm.w[nd];
-        wv.x += (double)x[2 * s];
-        wv.y += (double)x[2 * s + 1];
+        const vec2_t<TA> dx = sm.x[nd];
+        wv.x += (double)dx.x;
+        wv.y += (double)dx.y;
         sm.w[nd] = wv;
         if constexpr (REG) sm.w32[nd] = make_float2((float)wv.x, (float)wv.y);
       }
@@ -683,36 +821,33 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   }
   // the last residual norm used buffer (it & 1) and may still be read: use the other one
   block_sum<5, double>(Pv, sm.red + ((it + 1) & 1) * 512);
-  const double wq = 0.25 / ((double)n * n);  // |Omega| = 1
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sm.misc[4 + k] = Pv[k];
+  }
 
   // ---- tangent transfer (condensation) at the converged state
   int cond_total = 0, cond_max = 0;
   double Q[10];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) Q[k] = 0.0;
   const bool want_A = usable && !(a.flags & kFlagNoTangent) && a.A != nullptr;
   if (want_A) {
-    TA L[2][2][4];
-    build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, true, L);
-    vec2_t<TA>* X = reinterpret_cast<vec2_t<TA>*>(sm.stage);
+    build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb);
+    vec2_t<TA>* X = Xs;
     for (int c = 0; c < 4; ++c) {
-      TA b[4], x[4];
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        b[2 * s] = -L[s][0][c];
-        b[2 * s + 1] = -L[s][1][c];
+      TA b[4] = {TA(0), TA(0), TA(0), TA(0)};
+      if (o.active) {
+        const vec2_t<TA> b0 = Lb[c * NN + o.node[0]], b1 = Lb[c * NN + o.node[1]];
+        b[0] = b0.x;
+        b[1] = b0.y;
+        b[2] = b1.x;
+        b[3] = b1.y;
       }
-      if (o.node[0] == 0) b[0] = b[1] = TA(0);
       int pst = kStatusOk;
-      const int ci = pcg_pair<TA, REG>(S, o, Minv, b, x, (TA)a.cond_rtol, a.max_cond_cg, sm.p, redA, redB, &pst,
-                                        false);
+      const int ci = pcg_pair<TA, REG>(S, o, Minv, b, X + c * NN, (TA)a.cond_rtol, a.max_cond_cg, sm.p, redA, redB,
+                                        &pst, false);
       cond_total += ci;
       cond_max = ci > cond_max ? ci : cond_max;
       if (pst != kStatusOk && status == kStatusOk) status = pst;
-      if (o.active) {
-        X[c * NN + o.node[0]] = mk2<TA>(x[0], x[1]);
-        X[c * NN + o.node[1]] = mk2<TA>(x[2], x[3]);
-      }
     }
     __syncthreads();
     const vec2_t<TA>* wsrc;
@@ -721,6 +856,8 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
     } else {
       wsrc = reinterpret_cast<const vec2_t<TA>*>(sm.w);
     }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) Q[k] = 0.0;
     if (o.active) {
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
@@ -747,9 +884,10 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       a.iters[(size_t)qp * 4 + 3] = cond_max;
     }
     if (usable) {
+      const double wq = 0.25 / ((double)n * n);  // Gauss weight x det J; |Omega| = 1
 #pragma unroll
-      for (int k = 0; k < 4; ++k) a.P[(size_t)qp * 4 + k] = Pv[k] * wq;
-      if (want_W) a.W[qp] = Pv[4] * wq;
+      for (int k = 0; k < 4; ++k) a.P[(size_t)qp * 4 + k] = sm.misc[4 + k] * wq;
+      if (want_W) a.W[qp] = sm.misc[8] * wq;
       if (want_A) {
         int k = 0;
         for (int c = 0; c < 4; ++c)
