@@ -50,7 +50,8 @@ enum {
   FEHMM_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed */
   FEHMM_ERR_OOM = -3,          /* device allocation failed */
   FEHMM_ERR_STATE = -4,        /* call out of order (e.g. solve before bind_qps) */
-  FEHMM_ERR_UNSUPPORTED = -5   /* valid but unsupported configuration (e.g. odd 2D grid) */
+  FEHMM_ERR_UNSUPPORTED = -5,  /* valid but unsupported configuration (e.g. odd 2D grid) */
+  FEHMM_ERR_TOO_LARGE = -6     /* size beyond the fixed static scratch of the no-allocation entry */
 };
 
 enum { FEHMM_PREC_FP64 = 0, FEHMM_PREC_MIXED = 1 };
@@ -178,6 +179,36 @@ int fehmm_macro_csr(fehmm_ctx* ctx, const int32_t** rowptr, const int32_t** col,
 long long fehmm_launch_count(const fehmm_ctx* ctx);
 
 const char* fehmm_status_str(int code);
+
+/*
+ * No-allocation batched RVE solve, 2D, FP64 mode.  The paper has no counterpart: this is a
+ * deployment variant of fehmm_rve_solve for callers that cannot call cudaMalloc (runtimes
+ * that hand the library only pre-registered buffers, code running while a memory pool is
+ * torn down or resized, callers that need a footprint fixed at load time).  It allocates
+ * no device memory: the kernel's scratch (staged element tangents and the assembled
+ * stencil, 72*n*n doubles per block) and its work counter live in a file-scope static
+ * device array of fixed size (152 blocks x 72 x 256 doubles, about 22 MB), which every
+ * GPU that loads the library holds until the process exits.  It takes no context: the
+ * caller passes every input and output.
+ *   n_qp          number of quadrature points (RVE solves)
+ *   grid_n        elements per axis of every RVE: even, 2..16; larger -> FEHMM_ERR_TOO_LARGE
+ *   phase_per_qp  1: phase holds one map per qp; 0: one map shared by all
+ *   phase   device uint8 [phase_per_qp ? n_qp : 1][grid_n*grid_n], phase ids < 4
+ *   lame    device double [phase_per_qp ? n_qp : 1][4][2]: (lambda, mu) of each phase
+ *   w       device double [n_qp][grid_n*grid_n][2]: fluctuation start values in, results
+ *           out (the value at node 0 is taken as zero)
+ *   F, P, A, status, iters: as in fehmm_rve_solve (A may be NULL: no tangent)
+ *   opt     host; dim must be 2 and precision FEHMM_PREC_FP64; tolerances and caps used
+ * The first call on a device looks up the device address of the static array (with that
+ * device current); make that first call before any stream capture.  All calls share the
+ * array and the counter, which keep the last call's contents (the counter is cleared by
+ * each call on its stream): calls that overlap on the GPU (different streams, or another
+ * host thread) race and must be serialised by the caller.  Returns FEHMM_OK once enqueued.
+ */
+int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_per_qp, const uint8_t* phase,
+                                   const double* lame, double* w, const double* F, double* P,
+                                   double* A, int32_t* status, int32_t* iters,
+                                   const fehmm_options* opt, void* stream);
 
 #ifdef __cplusplus
 }

@@ -57,6 +57,7 @@ _SIGS = {
     "fehmm_macro_csr": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fehmm_launch_count": (ctypes.c_longlong, [_P]),
     "fehmm_status_str": (ctypes.c_char_p, [_I]),
+    "fehmm_rve2d_solve_fp64_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options), _P]),
 }
 
 

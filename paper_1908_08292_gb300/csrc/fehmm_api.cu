@@ -455,6 +455,7 @@ const char* fehmm_status_str(int code) {
     case FEHMM_ERR_OOM: return "out of device memory";
     case FEHMM_ERR_STATE: return "call out of order";
     case FEHMM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case FEHMM_ERR_TOO_LARGE: return "size exceeds the static scratch of the no-allocation entry point";
     default: return code > 0 ? "some RVE solves did not converge" : "unknown status";
   }
 }

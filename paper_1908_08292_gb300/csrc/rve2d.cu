@@ -694,17 +694,20 @@ __device__ __forceinline__ void element_transfer(int e, int n, const vec2_t<TA>*
   for (int k = 0; k < 10; ++k) Q[k] += (double)q[k];
 }
 
-template <typename TA>
+// kFixed: one grid size for the whole batch, arrays indexed arithmetically (qp -> RVE qp or 0,
+// fluctuation of qp at qp*2*n*n) instead of through the context's index tables.
+template <typename TA, bool kFixed = false>
 __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, TA* gscr) {
   constexpr bool REG = std::is_same<TA, float>::value;
   const int tid = threadIdx.x;
-  const int rv = a.qp_rve[qp];
-  const int n = a.rve_n[rv];
+  const int rv = kFixed ? (a.phase_per_qp ? qp : 0) : a.qp_rve[qp];
+  const int n = kFixed ? a.fixed_n : a.rve_n[rv];
   const int NN = n * n;
   const Own2D o = make_own(n);
-  const uint8_t* phase = a.phase + a.rve_phase_off[rv];
-  const double* w_in = a.w_in + a.qp_w_off[qp];
-  double* w_out = a.w_out + a.qp_w_off[qp];
+  const uint8_t* phase = a.phase + (kFixed ? (size_t)rv * n * n : (size_t)a.rve_phase_off[rv]);
+  const size_t w_off = kFixed ? (size_t)qp * 2 * n * n : (size_t)a.qp_w_off[qp];
+  const double* w_in = a.w_in + w_off;
+  double* w_out = a.w_out + w_off;
   double Fbd[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) Fbd[k] = a.F[(size_t)qp * 4 + k];
@@ -902,7 +905,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   __syncthreads();
 }
 
-template <typename TA>
+template <typename TA, bool kFixed = false>
 __global__ void __launch_bounds__(kThreads2D, 1) rve2d_kernel(const Rve2dArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem2D<TA> sm;
@@ -916,7 +919,7 @@ __global__ void __launch_bounds__(kThreads2D, 1) rve2d_kernel(const Rve2dArgs a)
     const int item = s_item;
     __syncthreads();
     if (item >= a.n_qp) break;
-    solve_item_2d<TA>(a, a.order[item], sm, gscr);
+    solve_item_2d<TA, kFixed>(a, kFixed ? item : a.order[item], sm, gscr);
   }
 }
 
@@ -944,6 +947,17 @@ cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStrea
     if (err != cudaSuccess) return err;
     rve2d_kernel<double><<<n_blocks, kThreads2D, smem, stream>>>(a);
   }
+  return cudaGetLastError();
+}
+
+// FP64 kernel over a fixed-layout batch with caller-provided scratch (the no-allocation
+// entry point in noalloc.cu supplies its static device array).
+cudaError_t rve2d_launch_fixed_fp64(const Rve2dArgs& a, int n_blocks, cudaStream_t stream) {
+  const size_t smem = rve2d_smem_bytes(a.nn_max, false);
+  cudaError_t err = cudaFuncSetAttribute(rve2d_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  rve2d_kernel<double, true><<<n_blocks, kThreads2D, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

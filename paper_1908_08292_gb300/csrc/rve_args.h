@@ -28,12 +28,15 @@ struct Rve2dArgs {
   void* scratch;                // per-block global scratch (FP64 mode)
   double newton_rtol, newton_atol, cg_rtol, cond_rtol;
   int max_newton, max_cg, max_cond_cg, flags;
+  int fixed_n;        // fixed-layout launches only: grid size of every RVE
+  int phase_per_qp;   // fixed-layout launches only: 1 = one phase map per qp, 0 = one shared
 };
 
 size_t rve2d_smem_bytes(int nn_max, bool mixed);
 size_t rve2d_scratch_bytes(int nn_max, bool mixed, int n_blocks);
 int rve2d_threads();
 cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream);
+cudaError_t rve2d_launch_fixed_fp64(const Rve2dArgs& a, int n_blocks, cudaStream_t stream);
 
 struct MacroArgs {
   int dim;
