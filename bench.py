@@ -5,7 +5,8 @@ Workload (one "step"): the 2D plane-strain FE-HMM workload with a 32x32 Q1 macro
 inclusion, stiffness ratio 5-50), mixed FP32/FP64 precision.  A step is one macro iteration
 of the hot path: Fbar at the quadrature points from the macro displacement, the batched RVE
 Newton solves with homogenised stress and tangent (starting from the committed fluctuations
-of the previous load step), and the macro residual/tangent assembly.
+of the previous load step), the macro residual/tangent assembly and the macro Newton
+correction (GPU CG on the assembled tangent).
 
 Value: RVE solves per second (whole job, all ranks).  Also reported: micro-DOF x Newton
 iterations per second.  `--impl reference` times the FP64 CPU oracle on a bounded sample
@@ -153,6 +154,7 @@ def run_gpu(args):
     ctx.add_rves(p.rve_n, p.rve_phase, p.rve_E, p.rve_nu)
     ctx.bind_qps(p.qp_rve)
     ctx.macro_create([_SIZE["macro"]] * 2)
+    ctx.macro_set_dirichlet(p.dirichlet_dofs, p.dirichlet_end)
     _, _, n_rows, nnz = ctx.macro_csr()
     u_h = torch.tensor(macro_affine_u(Fload), dtype=torch.float64).pin_memory()
     u = u_h.to(dev)
@@ -163,6 +165,8 @@ def run_gpu(args):
     it = torch.empty(n_qp, 4, dtype=torch.int32, device=dev)
     f = torch.empty(n_rows, dtype=torch.float64, device=dev)
     K = torch.empty(nnz, dtype=torch.float64, device=dev)
+    du = torch.empty(n_rows, dtype=torch.float64, device=dev)
+    info = torch.empty(3, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -170,6 +174,7 @@ def run_gpu(args):
         ctx.macro_qp_F(u, F)
         ctx.rve_solve(F, P, A, st, it, flags=fe.SOLVE_FROM_COMMITTED)
         ctx.macro_assemble(P, A, f, K)
+        ctx.macro_solve(K, f, du, info, rtol=1e-10)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -179,12 +184,11 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launches
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(5)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.zero_()
-            e0, e1, e2, e3 = ev[k]
+            e0, e1, e2, e3, e4 = ev[k]
             e0.record(stream)
             ctx.macro_qp_F(u, F)
             e1.record(stream)
@@ -192,9 +196,11 @@ def run_gpu(args):
             e2.record(stream)
             ctx.macro_assemble(P, A, f, K)
             e3.record(stream)
+            ctx.macro_solve(K, f, du, info, rtol=1e-10)
+            e4.record(stream)
         torch.cuda.synchronize()
     launches = ctx.launches - launches0
-    step_ms = [ev[k][0].elapsed_time(ev[k][3]) for k in range(args.steps)]
+    step_ms = [ev[k][0].elapsed_time(ev[k][4]) for k in range(args.steps)]
     rve_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
     t_step = sum(step_ms) / 1e3
     if world > 1:
@@ -218,7 +224,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         u.copy_(u_h, non_blocking=True)
         step()
-        f_h.copy_(f, non_blocking=True)
+        f_h.copy_(du, non_blocking=True)
         K_h.copy_(K, non_blocking=True)
         P_h.copy_(P, non_blocking=True)
         A_h.copy_(A, non_blocking=True)
@@ -247,7 +253,9 @@ def run_gpu(args):
         "pcg_iters_per_rve_mean": float(iters[:, 1].mean()), "transfer_pcg_iters_per_rve_mean": float(iters[:, 2].mean()),
         "phase_ms": {"macro_qp_F": statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)),
                      "rve_solve": statistics.mean(rve_ms),
-                     "macro_assemble": statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps))},
+                     "macro_assemble": statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)),
+                     "macro_solve": statistics.mean(ev[k][3].elapsed_time(ev[k][4]) for k in range(args.steps))},
+        "macro_cg_iters": int(info[1].item()),
         "roofline": {"kernel": "rve2d_kernel<float>", "bound": "alu",
                      "achieved": ach_eq, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s (FP32-equivalent)",
                      "frac": ach_eq / FP32_PEAK_TFLOPS, "traffic": None,

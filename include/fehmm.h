@@ -171,6 +171,31 @@ int fehmm_macro_qp_F(fehmm_ctx* ctx, const double* u, double* F, void* stream);
 int fehmm_macro_assemble(fehmm_ctx* ctx, const double* P, const double* A, double* f,
                          double* K_vals, void* stream);
 
+/* Dirichlet data of the macro problem (Eq. BCs, u = u_hat on the Dirichlet boundary): host
+ * arrays of n_fixed dof indices and their values at the end of the loading, copied.  Their
+ * rows and columns are removed from the macro solve (du = 0 there).  Default: none. */
+int fehmm_macro_set_dirichlet(fehmm_ctx* ctx, int n_fixed, const int32_t* dofs, const double* values);
+
+/* Start of a load step: u[dof] = scale * value on every Dirichlet dof (scale = load factor of
+ * the step) and, if du != NULL, du = 0.  u, du: device [n_rows]. */
+int fehmm_macro_apply_dirichlet(fehmm_ctx* ctx, double* u, double* du, double scale, void* stream);
+
+/* Macro Newton update u += du (device [n_rows] each; du is zero on Dirichlet dofs). */
+int fehmm_macro_update(fehmm_ctx* ctx, double* u, const double* du, void* stream);
+
+/*
+ * Macro Newton correction (the linearised HMM problem, Eq. L(GH)): solves K_ff du_f = -f_f
+ * with du = 0 on the Dirichlet dofs, by Jacobi-preconditioned CG in FP64 on the GPU
+ * (one cooperative launch; stops when the preconditioned residual norm falls below
+ * rtol times its initial value, or after max_it iterations).
+ *   K_vals device [nnz] (CSR order of fehmm_macro_csr), f device [n_rows], du device
+ *   [n_rows] (output), info device double[3] (output): |f_free|_2 (the macro convergence
+ *   measure, taken before the solve), CG iterations, status (0 converged, 1 cap,
+ *   2 non-positive curvature).
+ */
+int fehmm_macro_solve(fehmm_ctx* ctx, const double* K_vals, const double* f, double* du, double* info,
+                      double rtol, int max_it, void* stream);
+
 /* CSR pattern of the macro tangent (device pointers owned by the context). */
 int fehmm_macro_csr(fehmm_ctx* ctx, const int32_t** rowptr, const int32_t** col, int* n_rows,
                     int* nnz);

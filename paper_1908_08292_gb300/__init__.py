@@ -54,6 +54,10 @@ _SIGS = {
     "fehmm_macro_create": (_I, [_P, _P]),
     "fehmm_macro_qp_F": (_I, [_P, _P, _P, _P]),
     "fehmm_macro_assemble": (_I, [_P, _P, _P, _P, _P, _P]),
+    "fehmm_macro_set_dirichlet": (_I, [_P, _I, _P, _P]),
+    "fehmm_macro_apply_dirichlet": (_I, [_P, _P, _P, ctypes.c_double, _P]),
+    "fehmm_macro_update": (_I, [_P, _P, _P, _P]),
+    "fehmm_macro_solve": (_I, [_P, _P, _P, _P, _P, ctypes.c_double, _I, _P]),
     "fehmm_macro_csr": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fehmm_launch_count": (ctypes.c_longlong, [_P]),
     "fehmm_status_str": (ctypes.c_char_p, [_I]),
@@ -224,6 +228,31 @@ class Context:
         _check(lib().fehmm_macro_assemble(self._h, _dev(P, torch.float64, "P"), _dev(A, torch.float64, "A"),
                                           _dev(f, torch.float64, "f"), _dev(K_vals, torch.float64, "K_vals"),
                                           _stream(stream)), "macro_assemble")
+
+    def macro_set_dirichlet(self, dofs, values):
+        d = np.ascontiguousarray(dofs, dtype=np.int32)
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        if v.shape != d.shape:
+            raise FehmmError("dofs and values must have the same length")
+        _check(lib().fehmm_macro_set_dirichlet(self._h, int(d.size), d.ctypes.data if d.size else None,
+                                               v.ctypes.data if v.size else None), "macro_set_dirichlet")
+
+    def macro_apply_dirichlet(self, u, du, scale, stream=None):
+        import torch
+        _check(lib().fehmm_macro_apply_dirichlet(self._h, _dev(u, torch.float64, "u"), _dev(du, torch.float64, "du"),
+                                                 float(scale), _stream(stream)), "macro_apply_dirichlet")
+
+    def macro_update(self, u, du, stream=None):
+        import torch
+        _check(lib().fehmm_macro_update(self._h, _dev(u, torch.float64, "u"), _dev(du, torch.float64, "du"),
+                                        _stream(stream)), "macro_update")
+
+    def macro_solve(self, K_vals, f, du, info, rtol=1e-12, max_it=20000, stream=None):
+        """du = -K_ff^-1 f_f (du = 0 on Dirichlet dofs); info <- (|f_free|, iterations, status)."""
+        import torch
+        _check(lib().fehmm_macro_solve(self._h, _dev(K_vals, torch.float64, "K_vals"), _dev(f, torch.float64, "f"),
+                                       _dev(du, torch.float64, "du"), _dev(info, torch.float64, "info", 3),
+                                       float(rtol), int(max_it), _stream(stream)), "macro_solve")
 
     def macro_csr(self):
         """(rowptr, col, n_rows, nnz); rowptr/col are int32 device views owned by the context."""

@@ -46,6 +46,11 @@ struct fehmm_ctx {
   int32_t* d_blk_base = nullptr;
   int32_t* d_blk_stride = nullptr;
   int macro_rows = 0, macro_nnz = 0;
+  uint8_t* d_fixed = nullptr;   // Dirichlet mask of the macro dofs
+  int32_t* d_fixed_dofs = nullptr;
+  double* d_fixed_vals = nullptr;
+  int n_fixed = 0;
+  double* d_solve_work = nullptr;
   long long launches = 0;
 };
 
@@ -133,6 +138,10 @@ int fehmm_destroy(fehmm_ctx* c) {
   dfree(c->d_col);
   dfree(c->d_blk_base);
   dfree(c->d_blk_stride);
+  dfree(c->d_fixed);
+  dfree(c->d_fixed_dofs);
+  dfree(c->d_fixed_vals);
+  dfree(c->d_solve_work);
   delete c;
   return FEHMM_OK;
 }
@@ -400,6 +409,15 @@ int fehmm_macro_create(fehmm_ctx* c, const int32_t* n_el) {
     return rc;
   m.blk_base = c->d_blk_base;
   m.blk_stride = c->d_blk_stride;
+  std::vector<uint8_t> nofix((size_t)nn * d, 0);
+  if ((rc = dupload(c->d_fixed, nofix.data(), nofix.size()))) return rc;
+  dfree(c->d_solve_work);
+  const size_t wd = macro_solve_work_doubles(nn * d, macro_solve_blocks(c->num_sms));
+  if (cudaMalloc((void**)&c->d_solve_work, sizeof(double) * wd) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_solve_work = nullptr;
+    return FEHMM_ERR_OOM;
+  }
   c->macro = m;
   c->macro_rows = nn * d;
   c->macro_nnz = (int)pos;
@@ -433,6 +451,64 @@ int fehmm_macro_assemble(fehmm_ctx* c, const double* P, const double* A, double*
   const cudaError_t err = macro_assemble_launch(m, s, &launches);
   c->launches += launches;
   return err == cudaSuccess ? FEHMM_OK : FEHMM_ERR_CUDA;
+}
+
+int fehmm_macro_set_dirichlet(fehmm_ctx* c, int n_fixed, const int32_t* dofs, const double* values) {
+  if (!c || n_fixed < 0 || (n_fixed > 0 && (!dofs || !values))) return FEHMM_ERR_ARG;
+  if (!c->has_macro) return FEHMM_ERR_STATE;
+  std::vector<uint8_t> mask((size_t)c->macro_rows, 0);
+  for (int k = 0; k < n_fixed; ++k) {
+    if (dofs[k] < 0 || dofs[k] >= c->macro_rows) return FEHMM_ERR_ARG;
+    mask[dofs[k]] = 1;
+  }
+  int rc;
+  if ((rc = dupload(c->d_fixed, mask.data(), mask.size())) || (rc = dupload(c->d_fixed_dofs, dofs, (size_t)n_fixed)) ||
+      (rc = dupload(c->d_fixed_vals, values, (size_t)n_fixed)))
+    return rc;
+  c->n_fixed = n_fixed;
+  return FEHMM_OK;
+}
+
+int fehmm_macro_apply_dirichlet(fehmm_ctx* c, double* u, double* du, double scale, void* stream) {
+  if (!c || !u) return FEHMM_ERR_ARG;
+  if (!c->has_macro) return FEHMM_ERR_STATE;
+  if (macro_dirichlet_launch(u, du, c->macro_rows, c->d_fixed_dofs, c->d_fixed_vals, c->n_fixed, scale,
+                             (cudaStream_t)stream) != cudaSuccess)
+    return FEHMM_ERR_CUDA;
+  c->launches += 1;
+  return FEHMM_OK;
+}
+
+int fehmm_macro_update(fehmm_ctx* c, double* u, const double* du, void* stream) {
+  if (!c || !u || !du) return FEHMM_ERR_ARG;
+  if (!c->has_macro) return FEHMM_ERR_STATE;
+  if (macro_update_launch(u, du, c->macro_rows, (cudaStream_t)stream) != cudaSuccess) return FEHMM_ERR_CUDA;
+  c->launches += 1;
+  return FEHMM_OK;
+}
+
+int fehmm_macro_solve(fehmm_ctx* c, const double* K_vals, const double* f, double* du, double* info, double rtol,
+                      int max_it, void* stream) {
+  if (!c || !K_vals || !f || !du || !info || !(rtol > 0) || max_it <= 0) return FEHMM_ERR_ARG;
+  if (!c->has_macro) return FEHMM_ERR_STATE;
+  MacroSolveArgs a{};
+  a.n = c->macro_rows;
+  a.rowptr = c->d_rowptr;
+  a.col = c->d_col;
+  a.K = K_vals;
+  a.f = f;
+  a.fixed = c->d_fixed;
+  a.du = du;
+  a.work = c->d_solve_work;
+  a.out = info;
+  a.rtol = rtol;
+  a.max_it = max_it;
+  if (macro_solve_launch(a, macro_solve_blocks(c->num_sms), (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FEHMM_ERR_CUDA;
+  }
+  c->launches += 1;
+  return FEHMM_OK;
 }
 
 int fehmm_macro_csr(fehmm_ctx* c, const int32_t** rowptr, const int32_t** col, int* n_rows, int* nnz) {

@@ -151,7 +151,35 @@ __global__ void macro_assemble_kernel(const MacroArgs m, int color) {
   }
 }
 
+// u[dof_k] = scale * value_k on the Dirichlet dofs; du <- 0 everywhere (start of a load step)
+__global__ void macro_dirichlet_kernel(double* u, double* du, int n, const int32_t* dofs, const double* vals,
+                                       int n_fixed, double scale) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_fixed) u[dofs[t]] = scale * vals[t];
+  if (du)
+    for (int i = t; i < n; i += gridDim.x * blockDim.x) du[i] = 0.0;
+}
+
+// u += du (du is zero on the Dirichlet dofs)
+__global__ void macro_update_kernel(double* u, const double* du, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) u[t] += du[t];
+}
+
 }  // namespace
+
+cudaError_t macro_dirichlet_launch(double* u, double* du, int n, const int32_t* dofs, const double* vals, int n_fixed,
+                                   double scale, cudaStream_t stream) {
+  const int work = n_fixed > 0 ? n_fixed : 1;
+  const int blocks = (work + 255) / 256 > 0 ? (work + 255) / 256 : 1;
+  macro_dirichlet_kernel<<<blocks < 64 ? 64 : blocks, 256, 0, stream>>>(u, du, n, dofs, vals, n_fixed, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t macro_update_launch(double* u, const double* du, int n, cudaStream_t stream) {
+  macro_update_kernel<<<(n + 255) / 256, 256, 0, stream>>>(u, du, n);
+  return cudaGetLastError();
+}
 
 cudaError_t macro_qp_F_launch(const MacroArgs& m, cudaStream_t stream) {
   const int threads = 128, blocks = (m.n_qp + threads - 1) / threads;

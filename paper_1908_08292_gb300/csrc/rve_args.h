@@ -53,7 +53,28 @@ struct MacroArgs {
   const int32_t* blk_stride;  // [n_el][nen] row stride (entries) between the dim rows of node I
 };
 
+struct MacroSolveArgs {
+  int n;                    // rows (macro dofs)
+  const int32_t* rowptr;    // CSR pattern
+  const int32_t* col;
+  const double* K;          // CSR values
+  const double* f;          // macro residual
+  const uint8_t* fixed;     // [n] 1 = Dirichlet dof
+  double* du;               // [n] correction (output)
+  double* work;             // 4n + 2*blocks doubles
+  double* out;              // [3]: |f_free|_2, iterations, status (0 ok, 1 cap, 2 breakdown)
+  double rtol;
+  int max_it;
+};
+
+size_t macro_solve_work_doubles(int n, int blocks);
+int macro_solve_blocks(int num_sms);
+cudaError_t macro_solve_launch(const MacroSolveArgs& a, int blocks, cudaStream_t stream);
+
 cudaError_t macro_qp_F_launch(const MacroArgs& m, cudaStream_t stream);
+cudaError_t macro_dirichlet_launch(double* u, double* du, int n, const int32_t* dofs, const double* vals, int n_fixed,
+                                   double scale, cudaStream_t stream);
+cudaError_t macro_update_launch(double* u, const double* du, int n, cudaStream_t stream);
 cudaError_t macro_assemble_launch(const MacroArgs& m, cudaStream_t stream, int* launches);
 
 }  // namespace fehmm

@@ -1,0 +1,138 @@
+"""Two-level Newton load-step driver on the GPU: Algorithm 1 (nested) and Algorithm 2
+(alternating) of the paper, Sec. 5.
+
+Host control flow only: every step of a macro iteration is a library kernel launched through
+the C ABI — Dirichlet data and u += du (fehmm_macro_apply_dirichlet / fehmm_macro_update),
+Fbar at the quadrature points, the batched RVE solves, the macro assembly and the macro CG
+solve.  The host reads back three numbers per macro iteration (|f_free|, CG iterations, CG
+status) to decide convergence.
+
+Iteration structure of one load step (Sec. 5.1 / 5.2):
+  u[Dirichlet] <- t * u_hat, du <- 0
+  repeat:  u += du;  Fbar(u);  RVE solves (nested: to convergence; alternating: one micro
+           Newton iteration) starting from the last micro state (the committed one on the
+           first iteration: the warm start of Sec. 5.1);  assemble f, K;  solve K du = -f
+  until |f_free| <= max(rtol |f_free at the first iteration|, atol)
+The RVE pass of the last iteration is the "accuracy polish" of Sec. 5.1; the alternating
+scheme adds one more micro iteration at the converged u (Sec. 5.2).  Then commit.
+
+With graphs=True one macro iteration is captured into two CUDA graphs (first iteration of a
+step, later iterations) and replayed.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import SOLVE_FROM_COMMITTED, Context, FehmmError
+
+
+class LoadStepDriver:
+    def __init__(self, problem, precision=None, scheme="nested", graphs=False, macro_rtol=1e-10, macro_atol=1e-13,
+                 max_macro=40, solve_rtol=1e-12, **options):
+        import torch
+
+        if scheme not in ("nested", "alternating"):
+            raise FehmmError(f"unknown scheme {scheme}")
+        self.p = problem
+        self.scheme = scheme
+        self.macro_rtol, self.macro_atol, self.max_macro = macro_rtol, macro_atol, max_macro
+        self.solve_rtol = solve_rtol
+        precision = precision or problem.precision
+        opts = dict(newton_rtol=problem.newton_tol)
+        opts.update(options)
+        if scheme == "alternating":
+            opts["max_newton"] = 1
+        d = problem.dim
+        self.ctx = Context(d, precision, **opts)
+        self.ctx.add_rves(problem.rve_n, problem.rve_phase, problem.rve_E, problem.rve_nu)
+        self.ctx.bind_qps(problem.qp_rve)
+        self.ctx.macro_create(list(problem.macro_n))
+        self.ctx.macro_set_dirichlet(problem.dirichlet_dofs, problem.dirichlet_end)
+        _, _, n_rows, nnz = self.ctx.macro_csr()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n_qp = problem.n_qp
+        f64, i32 = torch.float64, torch.int32
+        self.u = torch.zeros(n_rows, dtype=f64, device=dev)
+        self.du = torch.zeros(n_rows, dtype=f64, device=dev)
+        self.F = torch.zeros(n_qp, d * d, dtype=f64, device=dev)
+        self.P = torch.zeros(n_qp, d * d, dtype=f64, device=dev)
+        self.A = torch.zeros(n_qp, d ** 4, dtype=f64, device=dev)
+        self.st = torch.zeros(n_qp, dtype=i32, device=dev)
+        self.it = torch.zeros(n_qp, 4, dtype=i32, device=dev)
+        self.f = torch.zeros(n_rows, dtype=f64, device=dev)
+        self.K = torch.zeros(nnz, dtype=f64, device=dev)
+        self.info = torch.zeros(3, dtype=f64, device=dev)
+        self.scale = 0.0
+        self.graphs = graphs
+        self._g = {}
+        self._warm = set()
+
+    # ------------------------------------------------------------ one iteration
+    def _iteration(self, first, solve=True):
+        c = self.ctx
+        c.macro_update(self.u, self.du)
+        c.macro_qp_F(self.u, self.F)
+        c.rve_solve(self.F, self.P, self.A, self.st, self.it, flags=SOLVE_FROM_COMMITTED if first else 0)
+        c.macro_assemble(self.P, self.A, self.f, self.K)
+        if solve:
+            c.macro_solve(self.K, self.f, self.du, self.info, rtol=self.solve_rtol)
+
+    def _run(self, first):
+        import torch
+        if not self.graphs:
+            self._iteration(first)
+            return
+        key = bool(first)
+        if key not in self._warm:  # run each variant once eagerly (module loading, attributes)
+            self._warm.add(key)
+            self._iteration(first)
+            return
+        if key not in self._g:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._iteration(first)
+            self._g[key] = g
+        self._g[key].replay()
+
+    # --------------------------------------------------------------- load step
+    def load_step(self, k):
+        """Run load step k (load factor k / n_steps); returns a record of the iterations."""
+        import torch
+        t0 = time.perf_counter()
+        self.scale = k / self.p.n_steps
+        self.ctx.macro_apply_dirichlet(self.u, self.du, self.scale)
+        hist, cg_its, micro = [], [], []
+        f0 = None
+        converged = False
+        for it in range(self.max_macro + 1):
+            self._run(first=(it == 0))
+            info = self.info.cpu().numpy()
+            status = self.st.cpu().numpy()
+            if np.any(status > 1):
+                raise FehmmError(f"RVE failure at step {k}, macro iteration {it}: statuses {np.unique(status)}")
+            micro.append(int(self.it[:, 0].sum().item()))
+            fn = float(info[0])
+            f0 = fn if f0 is None else f0
+            hist.append(fn)
+            cg_its.append(int(info[1]))
+            if fn <= max(self.macro_rtol * f0, self.macro_atol):
+                converged = True
+                break
+        # the last iteration's du is not applied: the state stays at the converged u
+        self.ctx.macro_apply_dirichlet(self.u, self.du, self.scale)
+        if self.scheme == "alternating":  # final micro iteration at the converged u (Sec. 5.2)
+            self._iteration(first=False, solve=False)
+            micro.append(int(self.it[:, 0].sum().item()))
+        self.ctx.commit()
+        torch.cuda.synchronize()
+        return {"step": k, "macro_iters": len(hist) - 1, "macro_hist": hist, "macro_cg": cg_its,
+                "micro_newton": micro, "converged": converged, "seconds": time.perf_counter() - t0}
+
+    def run(self, steps=None):
+        steps = self.p.n_steps if steps is None else steps
+        return [self.load_step(k) for k in range(1, steps + 1)]
+
+    def close(self):
+        self.ctx.close()

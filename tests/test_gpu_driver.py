@@ -1,0 +1,87 @@
+"""GPU load-step driver (Algorithms 1 and 2) and macro solve against the FP64 oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import driver as odriver
+from oracle import material as mat
+from oracle.macro import MacroMesh
+
+pytestmark = pytest.mark.gpu
+
+
+def test_macro_solve_matches_direct_solve():
+    import torch
+
+    import paper_1908_08292_gb300 as fe
+
+    n_el = (6, 5)
+    mesh = MacroMesh(n_el)
+    lam, mu = mat.lame(3.0, 0.3)
+    F = synth.random_F(501, mesh.n_qp, 2, 0.05)
+    P, A = mat.P_of_F(F, lam, mu), mat.A_of_F(F, lam, mu)
+    f_ref, K_ref = mesh.assemble(P, A)
+    fixed = np.nonzero(np.isclose(mesh.X[:, 0], 0.0))[0]
+    dofs = np.concatenate([2 * fixed, 2 * fixed + 1]).astype(np.int32)
+    dev = torch.device("cuda:0")
+    with fe.Context(2, "fp64") as ctx:
+        ctx.macro_create(n_el)
+        ctx.macro_set_dirichlet(dofs, np.zeros(dofs.size))
+        rowptr, col, nr, nnz = ctx.macro_csr()
+        Pt, At = torch.tensor(P.reshape(-1, 4), device=dev), torch.tensor(A.reshape(-1, 16), device=dev)
+        f = torch.zeros(nr, dtype=torch.float64, device=dev)
+        K = torch.zeros(nnz, dtype=torch.float64, device=dev)
+        du = torch.zeros(nr, dtype=torch.float64, device=dev)
+        info = torch.zeros(3, dtype=torch.float64, device=dev)
+        ctx.macro_assemble(Pt, At, f, K)
+        ctx.macro_solve(K, f, du, info, rtol=1e-13)
+        torch.cuda.synchronize()
+        du, info = du.cpu().numpy(), info.cpu().numpy()
+    free = np.setdiff1d(np.arange(mesh.n_dof), dofs)
+    ref = np.zeros(mesh.n_dof)
+    ref[free] = spla.spsolve(K_ref[free][:, free].tocsc(), -f_ref[free])
+    assert info[2] == 0
+    assert abs(info[0] - np.linalg.norm(f_ref[free])) < 1e-12 * np.linalg.norm(f_ref)
+    np.testing.assert_allclose(du, ref, atol=1e-9 * np.abs(ref).max())
+    assert np.all(du[dofs] == 0)
+
+
+@pytest.mark.parametrize("scheme", ["nested", "alternating"])
+def test_config1_load_steps_match_oracle(scheme):
+    from paper_1908_08292_gb300.driver import LoadStepDriver
+
+    p = synth.config1()
+    steps = 3
+    ref, mesh = odriver.run(p, scheme=scheme, steps_to_run=steps, micro_rtol=1e-12)
+    drv = LoadStepDriver(p, precision="fp64", scheme=scheme, newton_rtol=1e-12, newton_atol=1e-15, cg_rtol=1e-9,
+                         cond_rtol=1e-11)
+    try:
+        for k in range(1, steps + 1):
+            rec = drv.load_step(k)
+            assert rec["converged"]
+            u = drv.u.cpu().numpy()
+            P = drv.P.cpu().numpy().reshape(-1, 2, 2)
+            r = ref[k - 1]
+            assert np.abs(u - r["u"]).max() < 1e-9 * np.abs(r["u"]).max()
+            assert np.abs(P - r["P"]).max() < 1e-9 * np.abs(r["P"]).max()
+            assert abs(rec["macro_iters"] - r["macro_iters"]) <= (0 if scheme == "nested" else 1)
+    finally:
+        drv.close()
+
+
+def test_graph_replay_equals_eager():
+    from paper_1908_08292_gb300.driver import LoadStepDriver
+
+    p = synth.config1()
+    out = []
+    for graphs in (False, True):
+        drv = LoadStepDriver(p, precision="mixed", graphs=graphs)
+        try:
+            recs = [drv.load_step(k) for k in (1, 2)]
+            out.append((drv.u.cpu().numpy(), [r["macro_iters"] for r in recs]))
+        finally:
+            drv.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
