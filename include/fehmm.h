@@ -103,7 +103,7 @@ int fehmm_set_options(fehmm_ctx* ctx, const fehmm_options* opt);
 
 /*
  * Add n_rve microstructures (host arrays, copied).  grid_n[r]: elements per axis of RVE r
- * (2D: even, 2..32; 3D: see DESIGN).  phase: concatenation of the uint8 phase maps, RVE r
+ * (2D: even, 2..32; 3D: 2..16).  phase: concatenation of the uint8 phase maps, RVE r
  * holding grid_n[r]^dim entries in element order.  E, nu: [n_rve][n_phase] per-RVE
  * material table (Young's modulus, Poisson ratio; Lame constants are derived as in the
  * paper's Table of material parameters, Sec. 6), n_phase <= 4.  first_id (optional)

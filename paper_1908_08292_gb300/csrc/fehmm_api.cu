@@ -166,7 +166,7 @@ int fehmm_add_rves(fehmm_ctx* c, int n_rve, const int32_t* grid_n, const uint8_t
     const int n = grid_n[r];
     if (d == 2 && (n < 2 || n > 32)) return FEHMM_ERR_ARG;
     if (d == 2 && (n % 2) != 0) return FEHMM_ERR_UNSUPPORTED;
-    if (d == 3) return FEHMM_ERR_UNSUPPORTED;
+    if (d == 3 && (n < 2 || n > 16)) return FEHMM_ERR_ARG;
     for (int p = 0; p < n_phase; ++p) {
       const double e = E[(size_t)r * n_phase + p], v = nu[(size_t)r * n_phase + p];
       if (!(e > 0) || !(v > -1.0 && v < 0.5)) return FEHMM_ERR_ARG;
@@ -246,7 +246,8 @@ int fehmm_bind_qps(fehmm_ctx* c, int n_qp, const int32_t* rve_of_qp) {
       cudaMemset(c->d_w_comm, 0, sizeof(double) * total) != cudaSuccess)
     return FEHMM_ERR_CUDA;
   const int blocks = std::min(n_qp, c->num_sms);
-  const size_t sb = rve2d_scratch_bytes(nn_max, c->opt.precision == FEHMM_PREC_MIXED, blocks);
+  const bool mixed = c->opt.precision == FEHMM_PREC_MIXED;
+  const size_t sb = d == 2 ? rve2d_scratch_bytes(nn_max, mixed, blocks) : rve3d_scratch_bytes(nn_max, mixed, blocks);
   if (sb > c->scratch_bytes) {
     if (c->d_scratch) cudaFree(c->d_scratch);
     c->d_scratch = nullptr;
@@ -271,7 +272,6 @@ int fehmm_rve_solve(fehmm_ctx* c, const double* F, double* P, double* A, double*
   if (!(flags & FEHMM_SOLVE_NO_TANGENT) && !A) return FEHMM_ERR_ARG;
   if ((flags & FEHMM_SOLVE_ENERGY) && !W) return FEHMM_ERR_ARG;
   if (c->n_qp <= 0) return FEHMM_ERR_STATE;
-  if (c->opt.dim != 2) return FEHMM_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   Rve2dArgs a{};
   a.n_qp = c->n_qp;
@@ -303,7 +303,12 @@ int fehmm_rve_solve(fehmm_ctx* c, const double* F, double* P, double* A, double*
   a.flags = flags;
   if (cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;
   const int blocks = std::min(c->n_qp, c->num_sms);
-  if (rve2d_launch(a, c->opt.precision == FEHMM_PREC_MIXED, blocks, s) != cudaSuccess) return FEHMM_ERR_CUDA;
+  const bool mixed = c->opt.precision == FEHMM_PREC_MIXED;
+  const cudaError_t err = c->opt.dim == 2 ? rve2d_launch(a, mixed, blocks, s) : rve3d_launch(a, mixed, blocks, s);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return FEHMM_ERR_CUDA;
+  }
   c->launches += 1;
   return FEHMM_OK;
 }
@@ -412,7 +417,7 @@ int fehmm_macro_create(fehmm_ctx* c, const int32_t* n_el) {
   std::vector<uint8_t> nofix((size_t)nn * d, 0);
   if ((rc = dupload(c->d_fixed, nofix.data(), nofix.size()))) return rc;
   dfree(c->d_solve_work);
-  const size_t wd = macro_solve_work_doubles(nn * d, macro_solve_blocks(c->num_sms));
+  const size_t wd = macro_solve_work_doubles(nn * d, c->num_sms);
   if (cudaMalloc((void**)&c->d_solve_work, sizeof(double) * wd) != cudaSuccess) {
     cudaGetLastError();
     c->d_solve_work = nullptr;
@@ -503,7 +508,7 @@ int fehmm_macro_solve(fehmm_ctx* c, const double* K_vals, const double* f, doubl
   a.out = info;
   a.rtol = rtol;
   a.max_it = max_it;
-  if (macro_solve_launch(a, macro_solve_blocks(c->num_sms), (cudaStream_t)stream) != cudaSuccess) {
+  if (macro_solve_launch(a, macro_solve_blocks(c->num_sms, c->macro_nnz), (cudaStream_t)stream) != cudaSuccess) {
     cudaGetLastError();
     return FEHMM_ERR_CUDA;
   }

@@ -1,7 +1,8 @@
 // Macro Newton correction: K_ff du_f = -f_f with du = 0 on the Dirichlet dofs (the linearised
 // macro problem, Eq. L(GH) with the tangent of Eq. ModifiedBilinearForm-3 assembled as in
 // Eq. Assem_k_T_IK_mac).  Jacobi-preconditioned CG in FP64 over the CSR tangent, run as one
-// cooperative launch (one block per SM, all blocks co-resident; grid-wide barriers between the
+// cooperative launch (1024-thread blocks, about 64k nonzeros each, at most one per SM, all
+// co-resident; grid-wide barriers between the
 // sparse product, the inner products and the vector updates).  The inner products are summed
 // per block, then every block adds the block partials in the same order, so all blocks take
 // the same decisions.  The first output is |f_free|_2, the macro convergence measure.
@@ -16,7 +17,7 @@ namespace cg = cooperative_groups;
 namespace fehmm {
 namespace {
 
-constexpr int kSolveThreads = 256;
+constexpr int kSolveThreads = 1024;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -52,7 +53,8 @@ __global__ void __launch_bounds__(kSolveThreads) macro_pcg_kernel(const MacroSol
   double* z = a.work + n;
   double* p = a.work + 2 * (size_t)n;
   double* q = a.work + 3 * (size_t)n;
-  double* partial = a.work + 4 * (size_t)n;  // [gridDim.x]
+  double* dg = a.work + 4 * (size_t)n;        // Jacobi diagonal
+  double* partial = a.work + 5 * (size_t)n;  // [gridDim.x]
   double* partial2 = partial + gridDim.x;     // second buffer: alternate between reductions
   // diagonal for the Jacobi preconditioner
   double ff = 0.0, rz = 0.0;
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(kSolveThreads) macro_pcg_kernel(const MacroSol
     double d = 1.0;
     for (int k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k)
       if (a.col[k] == i) d = a.K[k];
+    dg[i] = d;
     const double ri = fixed ? 0.0 : -a.f[i];
     x[i] = 0.0;
     r[i] = ri;
@@ -101,10 +104,7 @@ __global__ void __launch_bounds__(kSolveThreads) macro_pcg_kernel(const MacroSol
         if (a.fixed[i]) continue;
         x[i] += alpha * p[i];
         r[i] -= alpha * q[i];
-        double d = 1.0;
-        for (int k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k)
-          if (a.col[k] == i) d = a.K[k];
-        z[i] = r[i] / d;
+        z[i] = r[i] / dg[i];
         rzn += r[i] * z[i];
       }
       rzn = grid_sum(rzn, partial2, sbuf, grid);
@@ -124,9 +124,15 @@ __global__ void __launch_bounds__(kSolveThreads) macro_pcg_kernel(const MacroSol
 
 }  // namespace
 
-size_t macro_solve_work_doubles(int n, int blocks) { return 4 * (size_t)n + 2 * (size_t)blocks; }
+size_t macro_solve_work_doubles(int n, int blocks) { return 5 * (size_t)n + 2 * (size_t)blocks; }
 
-int macro_solve_blocks(int num_sms) { return num_sms; }
+// Blocks for the cooperative solve: about 64k nonzeros per block (grid-wide barriers get more
+// expensive with every block, the sparse product needs enough of them), at most one per SM.
+int macro_solve_blocks(int num_sms, long long nnz) {
+  long long b = (nnz + 65535) / 65536;
+  if (b < 1) b = 1;
+  return (int)(b < num_sms ? b : num_sms);
+}
 
 cudaError_t macro_solve_launch(const MacroSolveArgs& a, int blocks, cudaStream_t stream) {
   void* args[] = {(void*)&a};

@@ -1,0 +1,729 @@
+// Batched periodic-RVE Newton solver for 3D (Hex8, 2x2x2 Gauss), one thread block per RVE,
+// persistent over a work queue of macro quadrature points (uneven grid sizes in one launch,
+// largest first).
+//
+// Method (paper Sec. 3.2-3.3): identical to the 2D kernel — R_a = sum wt detJ P(Fbar + Grad w)
+// Grad N_a (Eq. f_I^int, micro), Newton corrections K_T dw = -R (Eq. Saddlepoint-problem-Set-
+// of-eqs with periodic elimination, ch_3_eq_22), Pbar = <P> (Eq. Average-of-P-and-F) and the
+// tangent transfer Abar = <A> - L^T K^-1 L with L = dR/dFbar (the condensed form of the paper's
+// omega/|K_delta| T^T K T, Eq. k-mac-element-6; the two are checked equal in the oracle tests).
+//
+// GB300 layout:
+//  * 512 threads per block, one block per SM.  Elements are processed thread-strided; the
+//    nodal unknowns live in per-block global scratch (L2 resident), except the vector the
+//    tangent is applied to and its product, which live in shared memory.
+//  * Residual in FP64 per element (edge differences of the fluctuation; P = mu F + hb F^-T),
+//    element forces staged in global scratch and gathered per node (deterministic sums).
+//  * Tangent apply matrix-free in TA (FP32 in mixed mode): per Gauss point the kernel stores
+//    F^-T, hb and lam J^2 (11 values); the apply computes dF = Grad p from edge differences,
+//    dP = mu dF - hb Fit dF^T Fit + gm (Fit:dF) Fit and adds the element's nodal results to
+//    shared memory with float atomics.
+//  * Block-Jacobi with the 3x3 nodal diagonal blocks; PCG in the single-reduction form of
+//    Chronopoulos and Gear; truncated on negative curvature for Newton corrections.
+//  * Tangent transfer: L_c = apply of the element operator to the constant gradient E_c (the
+//    affine field), 9 PCG solves X_c = -K^-1 L_c, Abar = <A> + sym(L^T X), all sums in FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "fehmm_device.cuh"
+#include "rve_args.h"
+
+namespace fehmm {
+namespace {
+
+constexpr int kThreads3D = 512;
+constexpr int kQp3 = 11;  // per Gauss point: Fit (9), hb, gm
+
+__device__ __forceinline__ double g01(int g) { return g == 0 ? 0.21132486540518711775 : 0.78867513459481288225; }
+
+template <typename T>
+__device__ __forceinline__ T phi(int o, T t) { return o ? t : T(1) - t; }
+
+// 3x3 helpers (row-major, index 3*i + J)
+template <typename T>
+struct NH3 {
+  T Fit[9];
+  T J, hb, gm;
+};
+
+template <typename T>
+__device__ __forceinline__ NH3<T> nh3_eval(const T (&F)[9], T lam, T mu) {
+  NH3<T> r;
+  // cofactor matrix cof_iJ = dJ/dF_iJ; F^-T = cof / J
+  const T c00 = F[4] * F[8] - F[5] * F[7], c01 = F[5] * F[6] - F[3] * F[8], c02 = F[3] * F[7] - F[4] * F[6];
+  const T c10 = F[2] * F[7] - F[1] * F[8], c11 = F[0] * F[8] - F[2] * F[6], c12 = F[1] * F[6] - F[0] * F[7];
+  const T c20 = F[1] * F[5] - F[2] * F[4], c21 = F[2] * F[3] - F[0] * F[5], c22 = F[0] * F[4] - F[1] * F[3];
+  r.J = F[0] * c00 + F[1] * c01 + F[2] * c02;
+  const T iJ = T(1) / r.J;
+  r.Fit[0] = c00 * iJ;
+  r.Fit[1] = c01 * iJ;
+  r.Fit[2] = c02 * iJ;
+  r.Fit[3] = c10 * iJ;
+  r.Fit[4] = c11 * iJ;
+  r.Fit[5] = c12 * iJ;
+  r.Fit[6] = c20 * iJ;
+  r.Fit[7] = c21 * iJ;
+  r.Fit[8] = c22 * iJ;
+  const T J2 = r.J * r.J;
+  r.hb = T(0.5) * lam * (J2 - T(1)) - mu;
+  r.gm = lam * J2;
+  return r;
+}
+
+// dP = mu dF - hb Fit dF^T Fit + gm (Fit:dF) Fit
+template <typename T>
+__device__ __forceinline__ void tangent_action(const T* Fit, T hb, T gm, T mu, const T (&dF)[9], T (&dP)[9]) {
+  T U[9];  // U = dF^T Fit : U_LJ = sum_k dF_kL Fit_kJ
+#pragma unroll
+  for (int L = 0; L < 3; ++L)
+#pragma unroll
+    for (int J = 0; J < 3; ++J) U[3 * L + J] = dF[L] * Fit[J] + dF[3 + L] * Fit[3 + J] + dF[6 + L] * Fit[6 + J];
+  T a = T(0);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a += Fit[k] * dF[k];
+  const T ga = gm * a;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int J = 0; J < 3; ++J) {
+      const T t = Fit[3 * i + 0] * U[0 * 3 + J] + Fit[3 * i + 1] * U[1 * 3 + J] + Fit[3 * i + 2] * U[2 * 3 + J];
+      dP[3 * i + J] = mu * dF[3 * i + J] - hb * t + ga * Fit[3 * i + J];
+    }
+}
+
+struct Geo3 {
+  int n, NN;
+  __device__ __forceinline__ int node(int i, int j, int k) const {
+    return (i % n) + n * ((j % n) + n * (k % n));
+  }
+  // corner a = ox + 2 oy + 4 oz of element e
+  __device__ __forceinline__ void corners(int e, int (&nd)[8]) const {
+    const int i = e % n, j = (e / n) % n, k = e / (n * n);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) nd[a] = node(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+  }
+};
+
+// natural-coordinate gradient of a nodal field u[8][3] at (s,t,r): G[3*i + J] = du_i/dxi_J
+template <typename T>
+__device__ __forceinline__ void nat_grad(const T (&u)[8][3], T s, T t, T r, T (&G)[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int oz = 0; oz < 2; ++oz) {
+        const int a0 = 2 * oy + 4 * oz;
+        gx += (u[a0 + 1][i] - u[a0][i]) * phi(oy, t) * phi(oz, r);
+      }
+#pragma unroll
+    for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+      for (int oz = 0; oz < 2; ++oz) {
+        const int a0 = ox + 4 * oz;
+        gy += (u[a0 + 2][i] - u[a0][i]) * phi(ox, s) * phi(oz, r);
+      }
+#pragma unroll
+    for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy) {
+        const int a0 = ox + 2 * oy;
+        gz += (u[a0 + 4][i] - u[a0][i]) * phi(ox, s) * phi(oy, t);
+      }
+    G[3 * i + 0] = gx;
+    G[3 * i + 1] = gy;
+    G[3 * i + 2] = gz;
+  }
+}
+
+// y_a += c * sum_J S_iJ dN_a/dxi_J at (s,t,r) for the 8 corners
+template <typename T>
+__device__ __forceinline__ void nat_scatter(const T (&S)[9], T c, T s, T t, T r, T (&y)[8][3]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int ox = a & 1, oy = (a >> 1) & 1, oz = (a >> 2) & 1;
+    const T dx = (ox ? T(1) : T(-1)) * phi(oy, t) * phi(oz, r);
+    const T dy = (oy ? T(1) : T(-1)) * phi(ox, s) * phi(oz, r);
+    const T dz = (oz ? T(1) : T(-1)) * phi(ox, s) * phi(oy, t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[a][i] += c * (S[3 * i] * dx + S[3 * i + 1] * dy + S[3 * i + 2] * dz);
+  }
+}
+
+template <typename TA>
+struct Scratch3 {
+  // per-block global scratch, layout set by scratch3_layout
+  double* Rf;   // [24][NE] element forces (FP64)
+  TA* qpd;      // [kQp3][8][NE] Gauss-point material data
+  TA* x;        // [3][NN] PCG solution
+  TA* r;        // [3][NN]
+  TA* p;        // [3][NN]
+  TA* s;        // [3][NN]
+  TA* mi;       // [6][NN] inverted diagonal blocks (xx, xy, xz, yy, yz, zz)
+  TA* L;        // [9][3][NN] transfer right-hand sides
+};
+
+template <typename TA>
+__host__ __device__ inline size_t scratch3_bytes(int NN) {
+  const size_t b = sizeof(double) * 24 * (size_t)NN +
+                   sizeof(TA) * ((size_t)kQp3 * 8 * NN + 4 * 3 * (size_t)NN + 6 * (size_t)NN + 27 * (size_t)NN);
+  return (b + 255) & ~size_t(255);  // every block's scratch starts 256-byte aligned
+}
+
+template <typename TA>
+__device__ inline Scratch3<TA> scratch3_layout(unsigned char* base, int NN) {
+  Scratch3<TA> s;
+  s.Rf = reinterpret_cast<double*>(base);
+  TA* t = reinterpret_cast<TA*>(base + sizeof(double) * 24 * (size_t)NN);
+  s.qpd = t;
+  t += (size_t)kQp3 * 8 * NN;
+  s.x = t;
+  t += 3 * (size_t)NN;
+  s.r = t;
+  t += 3 * (size_t)NN;
+  s.p = t;
+  t += 3 * (size_t)NN;
+  s.s = t;
+  t += 3 * (size_t)NN;
+  s.mi = t;
+  t += 6 * (size_t)NN;
+  s.L = t;
+  return s;
+}
+
+// shared memory: vin [3][NN], vout [3][NN] (TA), reductions, lame, misc
+template <typename TA>
+__host__ __device__ inline size_t smem3_bytes(int NN) {
+  return sizeof(TA) * 6 * (size_t)NN + sizeof(double) * (2 * 512 + 2 * kMaxPhase + 128);
+}
+
+template <typename T>
+__device__ __forceinline__ void block_sum_n(T* v, int nv, T* buf) {
+  // nv <= 16 values; buf >= 32*16
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < nv; ++k) {
+    T x = warp_sum(v[k]);
+    if (lane == 0) buf[k * 32 + warp] = x;
+  }
+  __syncthreads();
+  for (int k = 0; k < nv; ++k) v[k] = warp_sum(lane < nw ? buf[k * 32 + lane] : T(0));
+  __syncthreads();
+}
+
+template <typename TA>
+struct Ctx3 {
+  Geo3 g;
+  int NE;
+  const uint8_t* phase;
+  const double* lame;  // shared [kMaxPhase][2]
+  Scratch3<TA> sc;
+  TA* vin;   // shared [3][NN]
+  TA* vout;  // shared [3][NN]
+  double* red;  // shared 2*512
+  double Fb[9];
+};
+
+// ---------------------------------------------------------------- FP64 residual
+template <typename TA>
+__device__ __noinline__ void residual3(const Ctx3<TA>& c, const double* w, double (&Psum)[9], double& bad) {
+  const int n = c.g.n;
+  const double ih = (double)n, cw = 0.125 / (ih * ih);  // wq / h = h^2 / 8
+  for (int e = threadIdx.x; e < c.NE; e += blockDim.x) {
+    int nd[8];
+    c.g.corners(e, nd);
+    double u[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = w[3 * nd[a] + i];
+    const int ph = c.phase[e];
+    const double lam = c.lame[2 * ph], mu = c.lame[2 * ph + 1];
+    double y[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) y[a][0] = y[a][1] = y[a][2] = 0.0;
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const double s = g01(q & 1), t = g01((q >> 1) & 1), r = g01(q >> 2);
+      double G[9], F[9];
+      nat_grad(u, s, t, r, G);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) F[k] = c.Fb[k] + ih * G[k];
+      const NH3<double> m = nh3_eval(F, lam, mu);
+      bad += m.J > 0.0 ? 0.0 : 1.0;
+      double P[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        P[k] = mu * F[k] + m.hb * m.Fit[k];
+        Psum[k] += P[k];
+      }
+      nat_scatter(P, cw, s, t, r, y);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) c.sc.Rf[(size_t)(3 * a + i) * c.NE + e] = y[a][i];
+  }
+}
+
+// gather element forces of node v: corner a of element (node - offset(a))
+template <typename TA>
+__device__ __forceinline__ void gather_R(const Ctx3<TA>& c, int v, double (&R)[3]) {
+  const int n = c.g.n;
+  const int i = v % n, j = (v / n) % n, k = v / (n * n);
+  R[0] = R[1] = R[2] = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int e = c.g.node(i + n - (a & 1), j + n - ((a >> 1) & 1), k + n - ((a >> 2) & 1));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) R[d] += c.sc.Rf[(size_t)(3 * a + d) * c.NE + e];
+  }
+}
+
+// ------------------------------------------------------- tangent data (TA)
+// Gauss-point data and nodal diagonal blocks (accumulated in shared memory vin|vout as
+// [6][NN]); optional FP64 accumulation of <A> (45 symmetric entries) for the transfer.
+template <typename TA, bool withA>
+__device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double* Asum /*[45] per thread, withA only*/) {
+  const int n = c.g.n, NN = c.g.NN;
+  TA* diag = c.vin;  // [6][NN] spans vin and vout
+  for (int v = threadIdx.x; v < 6 * NN; v += blockDim.x) diag[v] = TA(0);
+  __syncthreads();
+  const TA ih = (TA)n, wq = TA(0.125) / (ih * ih * ih);
+  for (int e = threadIdx.x; e < c.NE; e += blockDim.x) {
+    int nd[8];
+    c.g.corners(e, nd);
+    TA u[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = (TA)w[3 * nd[a] + i];
+    const int ph = c.phase[e];
+    const TA lam = (TA)c.lame[2 * ph], mu = (TA)c.lame[2 * ph + 1];
+    TA D[8][6];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) D[a][k] = TA(0);
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const TA s = (TA)g01(q & 1), t = (TA)g01((q >> 1) & 1), r = (TA)g01(q >> 2);
+      TA G[9], F[9];
+      nat_grad(u, s, t, r, G);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) F[k] = (TA)c.Fb[k] + ih * G[k];
+      const NH3<TA> m = nh3_eval(F, lam, mu);
+      TA* qd = c.sc.qpd + (size_t)q * c.NE + e;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) qd[(size_t)k * 8 * c.NE] = m.Fit[k];
+      qd[(size_t)9 * 8 * c.NE] = m.hb;
+      qd[(size_t)10 * 8 * c.NE] = m.gm;
+      // diagonal blocks: K_aa,ik = wq [mu |g_a|^2 d_ik + (gm - hb) v_a,i v_a,k], v_a = Fit g_a
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int ox = a & 1, oy = (a >> 1) & 1, oz = (a >> 2) & 1;
+        const TA gx = ih * (ox ? TA(1) : TA(-1)) * phi(oy, t) * phi(oz, r);
+        const TA gy = ih * (oy ? TA(1) : TA(-1)) * phi(ox, s) * phi(oz, r);
+        const TA gz = ih * (oz ? TA(1) : TA(-1)) * phi(ox, s) * phi(oy, t);
+        const TA v0 = m.Fit[0] * gx + m.Fit[1] * gy + m.Fit[2] * gz;
+        const TA v1 = m.Fit[3] * gx + m.Fit[4] * gy + m.Fit[5] * gz;
+        const TA v2 = m.Fit[6] * gx + m.Fit[7] * gy + m.Fit[8] * gz;
+        const TA mg = wq * mu * (gx * gx + gy * gy + gz * gz), cc = wq * (m.gm - m.hb);
+        D[a][0] += mg + cc * v0 * v0;
+        D[a][1] += cc * v0 * v1;
+        D[a][2] += cc * v0 * v2;
+        D[a][3] += mg + cc * v1 * v1;
+        D[a][4] += cc * v1 * v2;
+        D[a][5] += mg + cc * v2 * v2;
+      }
+      if constexpr (withA) {  // <A>_(iJ)(kL), upper triangle of the 9x9 major-symmetric matrix
+        int idx = 0;
+#pragma unroll
+        for (int p = 0; p < 9; ++p)
+#pragma unroll
+          for (int qq = p; qq < 9; ++qq) {
+            const int i = p / 3, J = p % 3, k = qq / 3, L = qq % 3;
+            TA val = -m.hb * m.Fit[3 * i + L] * m.Fit[3 * k + J] + m.gm * m.Fit[3 * i + J] * m.Fit[3 * k + L];
+            if (i == k && J == L) val += mu;
+            Asum[idx++] += (double)(wq * val);
+          }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) atomicAdd(&diag[k * NN + nd[a]], D[a][k]);
+  }
+  __syncthreads();
+  // invert the diagonal blocks (node 0 pinned: zero)
+  for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+    const TA a00 = diag[v], a01 = diag[NN + v], a02 = diag[2 * NN + v];
+    const TA a11 = diag[3 * NN + v], a12 = diag[4 * NN + v], a22 = diag[5 * NN + v];
+    const TA c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+    const TA c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+    const TA det = a00 * c00 + a01 * c01 + a02 * c02;
+    const TA id = v == 0 ? TA(0) : TA(1) / det;
+    c.sc.mi[v] = c00 * id;
+    c.sc.mi[NN + v] = c01 * id;
+    c.sc.mi[2 * NN + v] = c02 * id;
+    c.sc.mi[3 * NN + v] = c11 * id;
+    c.sc.mi[4 * NN + v] = c12 * id;
+    c.sc.mi[5 * NN + v] = c22 * id;
+  }
+  __syncthreads();
+}
+
+// Kept out of line so the element loop gets its own register allocation (no spills).
+// vout = K vin (mode 0) or vout = L_c: the element operator applied to the constant
+// gradient E_c (mode 1, c = 3k + L).  Pinned node 0 row zeroed.
+template <typename TA>
+__device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
+  const int n = c.g.n, NN = c.g.NN;
+  for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.vout[v] = TA(0);
+  __syncthreads();
+  const TA ih = (TA)n, cw = TA(0.125) / (ih * ih);
+  for (int e = threadIdx.x; e < c.NE; e += blockDim.x) {
+    int nd[8];
+    c.g.corners(e, nd);
+    TA u[8][3];
+    if (mode == 0) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) u[a][i] = c.vin[i * NN + nd[a]];
+    }
+    const TA mu = (TA)c.lame[2 * c.phase[e] + 1];
+    TA y[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) y[a][0] = y[a][1] = y[a][2] = TA(0);
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const TA s = (TA)g01(q & 1), t = (TA)g01((q >> 1) & 1), r = (TA)g01(q >> 2);
+      TA dF[9];
+      if (mode == 0) {
+        TA G[9];
+        nat_grad(u, s, t, r, G);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dF[k] = ih * G[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dF[k] = k == cidx ? TA(1) : TA(0);
+      }
+      const TA* qd = c.sc.qpd + (size_t)q * c.NE + e;
+      TA Fit[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Fit[k] = qd[(size_t)k * 8 * c.NE];
+      const TA hb = qd[(size_t)9 * 8 * c.NE], gm = qd[(size_t)10 * 8 * c.NE];
+      TA dP[9];
+      tangent_action(Fit, hb, gm, mu, dF, dP);
+      nat_scatter(dP, cw, s, t, r, y);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if (nd[a] == 0) continue;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) atomicAdd(&c.vout[i * NN + nd[a]], y[a][i]);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T div3(T a, T b) {
+  if constexpr (sizeof(T) == 4) {
+    return __fdividef(a, b);
+  } else {
+    return a / b;
+  }
+}
+
+// Chronopoulos-Gear PCG for K x = b; b given in sc.r on entry (overwritten), x in sc.x.
+template <typename TA>
+__device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* status) {
+  const int NN = c.g.NN;
+  TA* x = c.sc.x;
+  TA* r = c.sc.r;
+  TA* p = c.sc.p;
+  TA* s = c.sc.s;
+  const TA* mi = c.sc.mi;
+  TA* red = reinterpret_cast<TA*>(c.red);
+  auto precond_to_vin = [&]() {  // u = M^-1 r -> vin
+    for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+      const TA r0 = r[v], r1 = r[NN + v], r2 = r[2 * NN + v];
+      const TA m00 = mi[v], m01 = mi[NN + v], m02 = mi[2 * NN + v], m11 = mi[3 * NN + v], m12 = mi[4 * NN + v],
+               m22 = mi[5 * NN + v];
+      c.vin[v] = m00 * r0 + m01 * r1 + m02 * r2;
+      c.vin[NN + v] = m01 * r0 + m11 * r1 + m12 * r2;
+      c.vin[2 * NN + v] = m02 * r0 + m12 * r1 + m22 * r2;
+    }
+    __syncthreads();
+  };
+  auto dots = [&](TA& gam, TA& del) {
+    TA g = TA(0), d = TA(0);
+    for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
+      g += r[v] * c.vin[v];
+      d += c.vout[v] * c.vin[v];
+    }
+    TA vv[2] = {g, d};
+    block_sum_n<TA>(vv, 2, red);
+    gam = vv[0];
+    del = vv[1];
+  };
+  for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) x[v] = TA(0);
+  *status = kStatusOk;
+  precond_to_vin();
+  apply3(c, 0, 0);
+  TA gamma, delta;
+  dots(gamma, delta);
+  const TA gamma0 = gamma;
+  int it = 0;
+  if (!(gamma0 > TA(0))) return 0;
+  if (!(delta > TA(0))) {
+    if (truncate && delta < TA(0)) {
+      const TA a0 = div3(gamma, -delta);
+      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) x[v] = a0 * c.vin[v];
+      *status = kStatusNegCurv;
+    } else {
+      *status = kStatusPcgBreakdown;
+    }
+    __syncthreads();
+    return 0;
+  }
+  const TA stop = rtol * rtol * gamma0;
+  TA alpha = div3(gamma, delta), beta = TA(0);
+  for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
+    p[v] = c.vin[v];
+    s[v] = c.vout[v];
+  }
+  for (;;) {
+    if (it >= max_it) {
+      *status = kStatusPcgCap;
+      break;
+    }
+    for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
+      x[v] += alpha * p[v];
+      r[v] -= alpha * s[v];
+    }
+    __syncthreads();
+    precond_to_vin();
+    apply3(c, 0, 0);
+    TA gn, dn;
+    dots(gn, dn);
+    ++it;
+    if (gn <= stop) break;
+    beta = div3(gn, gamma);
+    const TA den = dn - beta * div3(gn, alpha);
+    if (!(den > TA(0))) {
+      *status = (truncate && den < TA(0)) ? kStatusNegCurv : kStatusPcgBreakdown;
+      break;
+    }
+    alpha = div3(gn, den);
+    gamma = gn;
+    for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
+      p[v] = c.vin[v] + beta * p[v];
+      s[v] = c.vout[v] + beta * s[v];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  return it;
+}
+
+template <typename TA>
+__device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, unsigned char* gscr) {
+  const int rv = a.qp_rve[qp];
+  const int n = a.rve_n[rv];
+  const int NN = n * n * n;
+  Ctx3<TA> c;
+  c.g.n = n;
+  c.g.NN = NN;
+  c.NE = NN;
+  c.phase = a.phase + a.rve_phase_off[rv];
+  c.vin = reinterpret_cast<TA*>(smem);
+  c.vout = c.vin + 3 * NN;
+  c.red = reinterpret_cast<double*>(smem + sizeof(TA) * 6 * (size_t)a.nn_max);
+  double* lame_s = c.red + 2 * 512;
+  double* misc = lame_s + 2 * kMaxPhase;
+  c.lame = lame_s;
+  c.sc = scratch3_layout<TA>(gscr, NN);
+  if (threadIdx.x < 2 * kMaxPhase) lame_s[threadIdx.x] = a.rve_lame[(size_t)rv * 2 * kMaxPhase + threadIdx.x];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c.Fb[k] = a.F[(size_t)qp * 9 + k];
+  const double* w_in = a.w_in + a.qp_w_off[qp];
+  double* w = a.w_out + a.qp_w_off[qp];
+  // the current fluctuation is kept in w_out (FP64, global); node 0 pinned to zero
+  for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) w[v] = v < 3 ? 0.0 : w_in[v];
+  __syncthreads();
+
+  int status = kStatusNewtonCap, it = 0, cg_total = 0;
+  double r0 = 0.0, Psum[9];
+  for (;;) {
+    double bad = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Psum[k] = 0.0;
+    residual3(c, w, Psum, bad);
+    __syncthreads();
+    double rr = 0.0;
+    for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+      double R[3];
+      gather_R(c, v, R);
+      if (v == 0) R[0] = R[1] = R[2] = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        rr += R[d] * R[d];
+        c.sc.r[d * NN + v] = (TA)(-R[d]);  // right-hand side of the Newton correction
+      }
+    }
+    double v2[2] = {rr, bad};
+    block_sum_n<double>(v2, 2, c.red);
+    const double rn = sqrt(v2[0]);
+    if (it == 0) r0 = rn;
+    if (v2[1] > 0.0) {
+      status = kStatusJNonPos;
+      break;
+    }
+    if (!isfinite(rn)) {
+      status = kStatusNonFinite;
+      break;
+    }
+    if (rn <= fmax(a.newton_rtol * r0, a.newton_atol)) {
+      status = kStatusOk;
+      break;
+    }
+    if (it >= a.max_newton) {
+      status = kStatusNewtonCap;
+      break;
+    }
+    tangent3<TA, false>(c, w, nullptr);
+    int pst = kStatusOk;
+    cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
+    if (pst == kStatusPcgBreakdown) {
+      status = kStatusPcgBreakdown;
+      break;
+    }
+    for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+      if (v == 0) continue;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) w[3 * v + d] += (double)c.sc.x[d * NN + v];
+    }
+    __syncthreads();
+    ++it;
+  }
+
+  const bool usable = (status == kStatusOk || status == kStatusNewtonCap);
+  double Pv[10];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Pv[k] = Psum[k];
+  Pv[9] = 0.0;
+  block_sum_n<double>(Pv, 10, c.red);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 10; ++k) misc[k] = Pv[k];
+
+  int cond_total = 0, cond_max = 0;
+  const bool want_A = usable && !(a.flags & kFlagNoTangent) && a.A != nullptr;
+  if (want_A) {
+    double As[45];
+#pragma unroll
+    for (int k = 0; k < 45; ++k) As[k] = 0.0;
+    tangent3<TA, true>(c, w, As);
+    // <A>: 45 FP64 sums in three reductions of 15
+    for (int part = 0; part < 3; ++part) block_sum_n<double>(As + 15 * part, 15, c.red);
+    // right-hand sides L_c (c = 3k + L) stored [c][3][NN]
+    for (int cc = 0; cc < 9; ++cc) {
+      apply3(c, 1, cc);
+      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.L[(size_t)cc * 3 * NN + v] = c.vout[v];
+    }
+    __syncthreads();
+    // LX[c][c'] = L_c . X_c', X_c' = -K^-1 L_c'  (kept in shared memory: misc[16 + 9c + c'])
+    double* LX = misc + 16;
+    for (int cp = 0; cp < 9; ++cp) {
+      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.r[v] = -c.sc.L[(size_t)cp * 3 * NN + v];
+      __syncthreads();
+      int pst = kStatusOk;
+      const int ci = pcg3(c, (TA)a.cond_rtol, a.max_cond_cg, false, &pst);
+      cond_total += ci;
+      cond_max = ci > cond_max ? ci : cond_max;
+      if (pst != kStatusOk && status == kStatusOk) status = pst;
+      double col[9];
+#pragma unroll
+      for (int cc = 0; cc < 9; ++cc) col[cc] = 0.0;
+      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
+        const double xv = (double)c.sc.x[v];
+#pragma unroll
+        for (int cc = 0; cc < 9; ++cc) col[cc] += (double)c.sc.L[(size_t)cc * 3 * NN + v] * xv;
+      }
+      block_sum_n<double>(col, 9, c.red);
+      if (threadIdx.x == 0)
+        for (int cc = 0; cc < 9; ++cc) LX[9 * cc + cp] = col[cc];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int idx = 0;
+      for (int p = 0; p < 9; ++p)
+        for (int q = p; q < 9; ++q) {
+          const double v = As[idx++] + 0.5 * (LX[9 * p + q] + LX[9 * q + p]);
+          a.A[(size_t)qp * 81 + p * 9 + q] = v;
+          a.A[(size_t)qp * 81 + q * 9 + p] = v;
+        }
+    }
+  }
+  if (threadIdx.x == 0) {
+    a.status[qp] = status;
+    if (a.iters) {
+      a.iters[(size_t)qp * 4 + 0] = it;
+      a.iters[(size_t)qp * 4 + 1] = cg_total;
+      a.iters[(size_t)qp * 4 + 2] = cond_total;
+      a.iters[(size_t)qp * 4 + 3] = cond_max;
+    }
+    if (usable) {
+      const double wq = 0.125 / ((double)n * n * n);
+      for (int k = 0; k < 9; ++k) a.P[(size_t)qp * 9 + k] = misc[k] * wq;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(kThreads3D, 1) rve3d_kernel(const Rve2dArgs a) {
+  extern __shared__ __align__(16) unsigned char smem3[];
+  __shared__ int s_item;
+  unsigned char* gscr = reinterpret_cast<unsigned char*>(a.scratch) + (size_t)blockIdx.x * scratch3_bytes<TA>(a.nn_max);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= a.n_qp) break;
+    solve_item_3d<TA>(a, a.order[item], smem3, gscr);
+  }
+}
+
+}  // namespace
+
+size_t rve3d_smem_bytes(int nn_max, bool mixed) {
+  return mixed ? smem3_bytes<float>(nn_max) : smem3_bytes<double>(nn_max);
+}
+
+size_t rve3d_scratch_bytes(int nn_max, bool mixed, int n_blocks) {
+  return (mixed ? scratch3_bytes<float>(nn_max) : scratch3_bytes<double>(nn_max)) * (size_t)n_blocks;
+}
+
+cudaError_t rve3d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream) {
+  const size_t smem = rve3d_smem_bytes(a.nn_max, mixed);
+  cudaError_t err;
+  if (mixed) {
+    err = cudaFuncSetAttribute(rve3d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    rve3d_kernel<float><<<n_blocks, kThreads3D, smem, stream>>>(a);
+  } else {
+    err = cudaFuncSetAttribute(rve3d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    rve3d_kernel<double><<<n_blocks, kThreads3D, smem, stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fehmm

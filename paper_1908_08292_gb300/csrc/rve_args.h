@@ -37,6 +37,9 @@ size_t rve2d_scratch_bytes(int nn_max, bool mixed, int n_blocks);
 int rve2d_threads();
 cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream);
 cudaError_t rve2d_launch_fixed_fp64(const Rve2dArgs& a, int n_blocks, cudaStream_t stream);
+size_t rve3d_smem_bytes(int nn_max, bool mixed);
+size_t rve3d_scratch_bytes(int nn_max, bool mixed, int n_blocks);
+cudaError_t rve3d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream);
 
 struct MacroArgs {
   int dim;
@@ -61,14 +64,14 @@ struct MacroSolveArgs {
   const double* f;          // macro residual
   const uint8_t* fixed;     // [n] 1 = Dirichlet dof
   double* du;               // [n] correction (output)
-  double* work;             // 4n + 2*blocks doubles
+  double* work;             // 5n + 2*blocks doubles
   double* out;              // [3]: |f_free|_2, iterations, status (0 ok, 1 cap, 2 breakdown)
   double rtol;
   int max_it;
 };
 
 size_t macro_solve_work_doubles(int n, int blocks);
-int macro_solve_blocks(int num_sms);
+int macro_solve_blocks(int num_sms, long long nnz);
 cudaError_t macro_solve_launch(const MacroSolveArgs& a, int blocks, cudaStream_t stream);
 
 cudaError_t macro_qp_F_launch(const MacroArgs& m, cudaStream_t stream);

@@ -1,0 +1,68 @@
+"""Parity of the CUDA 3D (Hex8) RVE batch with the FP64 oracle.
+
+Tolerances as in 2D (relative Frobenius norm per quadrature point, P floored at 1e-3 x the matrix
+Young's modulus): FP64 mode 1e-10 on P and A, mixed mode 1e-5."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import material as mat
+from oracle.rve import PeriodicRVE
+from gpu_harness import gpu_batch, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+STRICT = dict(newton_rtol=1e-13, newton_atol=1e-15, cg_rtol=1e-9, cond_rtol=1e-11)
+
+
+def check(out, refs, tol):
+    for q, ref in enumerate(refs):
+        assert out["status"][q] == 0, (q, out["status"][q])
+        eP = rel_err(out["P"][q], ref["P"], 1e-3)
+        eA = rel_err(out["A"][q], ref["A"], 1e-3)
+        assert eP < tol and eA < tol, (q, eP, eA)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_uneven_small_sizes_one_launch(precision):
+    """n = 2 (the 27-point neighbourhood wraps onto itself), 3 (odd), 4 and 6 in one launch."""
+    sizes = [2, 3, 4, 6]
+    u = synth.uniform(601, np.arange(len(sizes)), 4)
+    phases, E, nu = [], [], []
+    for k, n in enumerate(sizes):
+        phases.append(synth.phase_from_inclusions(n, 3, [u[k, :3]], [0.2 + 0.15 * u[k, 3]]))
+        E.append([1.0, 10.0])
+        nu.append([0.3, 0.25])
+    qp_rve = np.array([3, 0, 1, 2, 3, 2])
+    Fs = synth.random_F(602, len(qp_rve), 3, 0.08)
+    opts = STRICT if precision == "fp64" else {}
+    out = gpu_batch(3, precision, sizes, phases, E, nu, qp_rve, Fs, **opts)
+    refs = [PeriodicRVE(sizes[r], 3, phases[r], E[r], nu[r]).solve(F, rtol=1e-14, atol=1e-16)
+            for r, F in zip(qp_rve, Fs)]
+    check(out, refs, TOL[precision])
+    for q, r in enumerate(qp_rve):
+        assert np.abs(out["w"][q] - refs[q]["w"]).max() < (1e-10 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config3_generator_rves(precision):
+    """8^3 RVEs of the config-3 generator (1-4 spheres, ratio 10) along its uniaxial load path."""
+    p = synth.config3(macro=1, sizes=(8,), n_rve=3)
+    Fs = np.array([np.diag([1.0 + s, 1.0 - 0.3 * s, 1.0 - 0.3 * s]) for s in (0.02, 0.1, 0.2)])
+    opts = STRICT if precision == "fp64" else {}
+    out = gpu_batch(3, precision, p.rve_n, p.rve_phase, p.rve_E, p.rve_nu, np.arange(3), Fs, **opts)
+    refs = [PeriodicRVE(8, 3, p.rve_phase[r], p.rve_E[r], p.rve_nu[r]).solve(Fs[r], rtol=1e-14, atol=1e-16)
+            for r in range(3)]
+    check(out, refs, TOL[precision])
+
+
+def test_homogeneous_rve_is_pointwise_law_3d():
+    n = 4
+    Fs = synth.random_F(603, 2, 3, 0.1)
+    out = gpu_batch(3, "fp64", [n], [np.zeros(n ** 3, np.uint8)], [[2.0, 2.0]], [[0.3, 0.3]], [0, 0], Fs, **STRICT)
+    lam, mu = mat.lame(2.0, 0.3)
+    for q in range(2):
+        assert out["status"][q] == 0 and out["iters"][q][0] == 0
+        np.testing.assert_allclose(out["P"][q], mat.P_of_F(Fs[q], lam, mu), atol=1e-13)
+        np.testing.assert_allclose(out["A"][q], mat.A_of_F(Fs[q], lam, mu), atol=1e-12)
