@@ -30,9 +30,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RVE solves/s (micro-DOF*Newton-iter/s reported alongside)"
-_SIZE = {"macro": 32}
+_SIZE = {"macro": 32, "workload": "c2"}
 UNIT = "RVE solves/s"
 MACRO, RVE_N, N_STEPS = 32, 32, 20
+MACRO_C3, N_STEPS_C3 = 8, 10
 
 # Algorithmic operation counts per unit of the 2D mixed kernel (derivation in the design doc,
 # counted from the kernel source, an FMA counting 2).
@@ -40,12 +41,23 @@ FP64_FLOP_PER_ELEMENT_RESIDUAL = 290.0   # F, J, F^-T, P and nodal forces at 4 G
 FP32_FLOP_PER_ELEMENT_TANGENT = 1350.0   # 8x8 element tangent at 4 Gauss points + stencil gather
 FP32_FLOP_PER_NODE_PCG_ITER = 100.0      # 9-block 2x2 stencil apply + vector updates + 2 dots
 FP32_FLOP_PER_ELEMENT_TRANSFER = 1500.0  # energy form of the tangent transfer (4 unit gradients)
+FP64_FLOP_PER_ELEMENT_RESIDUAL_3D = 2640.0   # Hex8: 8 Gauss points x (grad, F^-T, P, nodal forces)
+FP32_FLOP_PER_ELEMENT_TANGENT_3D = 4200.0    # Gauss-point data + 3x3 diagonal blocks
+FP32_FLOP_PER_ELEMENT_APPLY_3D = 4000.0      # matrix-free apply: grad, dP = A:dF, nodal scatter
+FP32_FLOP_PER_NODE_PCG_ITER_3D = 30.0        # preconditioner + vector updates + dots
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
 
 
 def workload_config(step_index):
     MACRO = _SIZE["macro"]
+    if _SIZE["workload"] == "c3":
+        return {"workload": f"3D FE-HMM macro {MACRO}^3 Hex8 ({MACRO ** 3 * 8} qps), one periodic Hex8 RVE per qp "
+                            f"of 8^3/12^3/16^3 elements (uniform draw), 1-4 spheres (volume fraction 0.1-0.3, "
+                            f"stiffness ratio 10), neo-Hookean, mixed FP32/FP64, uneven batch in one persistent "
+                            f"launch, macro iteration 1 of load step {step_index}/{N_STEPS_C3} (uniaxial to 20%)",
+                "n_qp": MACRO ** 3 * 8, "rve_grid": "8/12/16 mixed", "load_step": step_index,
+                "l2": "flushed (256 MB write) between timed steps"}
     return {"workload": f"2D plane-strain FE-HMM macro {MACRO}x{MACRO} Q1 ({MACRO * MACRO * 4} qps), "
                         f"one {RVE_N}x{RVE_N} Q1 periodic RVE per qp (random circular inclusion r~U(0.15,0.35), "
                         f"E ratio log-U[5,50]), neo-Hookean, mixed FP32/FP64, macro iteration 1 of load step "
@@ -110,7 +122,12 @@ class ClockSampler:
 
 
 def build_problem(step_index):
+    """The workload and the macro deformation gradient of the affine first iterate of the step."""
     import synth
+    if _SIZE["workload"] == "c3":
+        p = synth.config3(macro=_SIZE["macro"])
+        F = np.diag([1.0 + 0.2 * step_index / N_STEPS_C3, 1.0, 1.0])
+        return p, F
     p = synth.config2(macro=_SIZE["macro"], rve=RVE_N)
     lam = step_index / N_STEPS
     F = np.eye(2) + lam * (p.extra["F_end"] - np.eye(2))
@@ -118,10 +135,24 @@ def build_problem(step_index):
 
 
 def macro_affine_u(F):
+    """u = (F - I) X at the macro nodes (x fastest)."""
     MACRO = _SIZE["macro"]
-    X = np.stack(np.meshgrid(np.arange(MACRO + 1) / MACRO, np.arange(MACRO + 1) / MACRO, indexing="xy"), -1)
-    X = X.reshape(-1, 2)
-    return (X @ (F - np.eye(2)).T).reshape(-1)
+    d = F.shape[0]
+    ax = np.arange(MACRO + 1) / MACRO
+    X = np.stack(np.meshgrid(*([ax] * d), indexing="ij"), -1)
+    X = X.transpose(*range(d - 1, -1, -1), d).reshape(-1, d)
+    return (X @ (F - np.eye(d)).T).reshape(-1)
+
+
+def flops_3d(p, iters):
+    """FP64 and FP32 algorithmic flops of one 3D batch solve from the per-qp iteration counts."""
+    el = np.array([int(p.rve_n[r]) ** 3 for r in p.qp_rve], dtype=np.float64)
+    newton = iters[:, 0].astype(np.float64)
+    cg = iters[:, 1].astype(np.float64) + iters[:, 2].astype(np.float64)
+    f64 = ((newton + 1) * FP64_FLOP_PER_ELEMENT_RESIDUAL_3D * el).sum()
+    f32 = ((newton + 1) * FP32_FLOP_PER_ELEMENT_TANGENT_3D * el
+           + (cg + 9) * (FP32_FLOP_PER_ELEMENT_APPLY_3D + FP32_FLOP_PER_NODE_PCG_ITER_3D) * el).sum()
+    return f64, f32
 
 
 def flops_2d(n, iters):
@@ -150,17 +181,18 @@ def run_gpu(args):
     p, Fload = build_problem(args.step_index)
     n_qp = p.n_qp
     opts = {k: v for k, v in (("cg_rtol", args.cg_rtol), ("cond_rtol", args.cond_rtol)) if v is not None}
-    ctx = fe.Context(2, "mixed", **opts)
+    d = p.dim
+    ctx = fe.Context(d, "mixed", **opts)
     ctx.add_rves(p.rve_n, p.rve_phase, p.rve_E, p.rve_nu)
     ctx.bind_qps(p.qp_rve)
-    ctx.macro_create([_SIZE["macro"]] * 2)
+    ctx.macro_create([_SIZE["macro"]] * d)
     ctx.macro_set_dirichlet(p.dirichlet_dofs, p.dirichlet_end)
     _, _, n_rows, nnz = ctx.macro_csr()
     u_h = torch.tensor(macro_affine_u(Fload), dtype=torch.float64).pin_memory()
     u = u_h.to(dev)
-    F = torch.empty(n_qp, 4, dtype=torch.float64, device=dev)
-    P = torch.empty(n_qp, 4, dtype=torch.float64, device=dev)
-    A = torch.empty(n_qp, 16, dtype=torch.float64, device=dev)
+    F = torch.empty(n_qp, d * d, dtype=torch.float64, device=dev)
+    P = torch.empty(n_qp, d * d, dtype=torch.float64, device=dev)
+    A = torch.empty(n_qp, d ** 4, dtype=torch.float64, device=dev)
     st = torch.empty(n_qp, dtype=torch.int32, device=dev)
     it = torch.empty(n_qp, 4, dtype=torch.int32, device=dev)
     f = torch.empty(n_rows, dtype=torch.float64, device=dev)
@@ -214,8 +246,8 @@ def run_gpu(args):
     # ---- end-to-end through the public API with host buffers (H2D of u, D2H of results)
     f_h = torch.empty(n_rows, dtype=torch.float64).pin_memory()
     K_h = torch.empty(nnz, dtype=torch.float64).pin_memory()
-    P_h = torch.empty(n_qp, 4, dtype=torch.float64).pin_memory()
-    A_h = torch.empty(n_qp, 16, dtype=torch.float64).pin_memory()
+    P_h = torch.empty(n_qp, d * d, dtype=torch.float64).pin_memory()
+    A_h = torch.empty(n_qp, d ** 4, dtype=torch.float64).pin_memory()
     s_h = torch.empty(n_qp, dtype=torch.int32).pin_memory()
     e2e_ms = []
     for k in range(max(1, args.steps)):
@@ -232,15 +264,16 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     h2d = u_h.numel() * 8
-    d2h = (n_rows + nnz + n_qp * 20) * 8 + n_qp * 4
+    d2h = (n_rows + nnz + n_qp * (d * d + d ** 4)) * 8 + n_qp * 4
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     n_total = n_qp * world
     value = n_total / (t_step / args.steps)
-    dof_iter = float((2 * RVE_N * RVE_N * iters[:, 0].astype(np.float64)).sum()) * world / (t_step / args.steps)
-    f64, f32 = flops_2d(RVE_N, iters)
+    dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve], dtype=np.float64)
+    dof_iter = float((dofs * iters[:, 0].astype(np.float64)).sum()) * world / (t_step / args.steps)
+    f64, f32 = flops_2d(RVE_N, iters) if d == 2 else flops_3d(p, iters)
     t_rve = statistics.mean(rve_ms) / 1e3
     ach_eq = (f32 + f64 * FP32_PEAK_TFLOPS / FP64_PEAK_TFLOPS) / t_rve / 1e12
     out = {
@@ -256,7 +289,7 @@ def run_gpu(args):
                      "macro_assemble": statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)),
                      "macro_solve": statistics.mean(ev[k][3].elapsed_time(ev[k][4]) for k in range(args.steps))},
         "macro_cg_iters": int(info[1].item()),
-        "roofline": {"kernel": "rve2d_kernel<float>", "bound": "alu",
+        "roofline": {"kernel": f"rve{d}d_kernel<float>", "bound": "alu",
                      "achieved": ach_eq, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s (FP32-equivalent)",
                      "frac": ach_eq / FP32_PEAK_TFLOPS, "traffic": None,
                      "fp64_tflops": f64 / t_rve / 1e12, "fp32_tflops": f32 / t_rve / 1e12,
@@ -282,7 +315,7 @@ def cpu_baseline(budget_s, step_index=1):
     done = 0
     while time.perf_counter() - t0 < budget_s and done < p.n_qp:
         r = p.qp_rve[done]
-        PeriodicRVE(RVE_N, 2, p.rve_phase[r], p.rve_E[r], p.rve_nu[r]).solve(Fload, rtol=1e-10)
+        PeriodicRVE(int(p.rve_n[r]), p.dim, p.rve_phase[r], p.rve_E[r], p.rve_nu[r]).solve(Fload, rtol=1e-10)
         done += 1
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -302,7 +335,7 @@ def run_reference(args):
         for j in range(per_step):
             q = (k * per_step + j) % p.n_qp
             r = p.qp_rve[q]
-            PeriodicRVE(RVE_N, 2, p.rve_phase[r], p.rve_E[r], p.rve_nu[r]).solve(Fload, rtol=1e-10)
+            PeriodicRVE(int(p.rve_n[r]), p.dim, p.rve_phase[r], p.rve_E[r], p.rve_nu[r]).solve(Fload, rtol=1e-10)
 
     for k in range(args.warmup):
         step(k)
@@ -334,9 +367,12 @@ def main():
     ap.add_argument("--ref-rves-per-step", type=int, default=4)
     ap.add_argument("--cg-rtol", type=float, default=None, help="override the Newton-correction PCG tolerance")
     ap.add_argument("--cond-rtol", type=float, default=None, help="override the tangent-transfer PCG tolerance")
-    ap.add_argument("--macro", type=int, default=MACRO, help="macro elements per axis (profiling runs use less)")
+    ap.add_argument("--macro", type=int, default=None, help="macro elements per axis (profiling runs use less)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: 2D 4096 RVEs of 32x32 (default, the headline); c3: 3D 4096 uneven Hex8 RVEs")
     args = ap.parse_args()
-    _SIZE["macro"] = args.macro
+    _SIZE["workload"] = args.workload
+    _SIZE["macro"] = args.macro if args.macro is not None else (MACRO_C3 if args.workload == "c3" else MACRO)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -35,7 +35,40 @@ namespace fehmm {
 namespace {
 
 constexpr int kThreads3D = 512;
-constexpr int kQp3 = 11;  // per Gauss point: Fit (9), hb, gm
+constexpr int kQp3 = 12;  // per Gauss point: Fit (9), hb, gm, padding (vector loads)
+
+// Gauss-point data layout [8 qp][12 values][NE] grouped into 4-wide vectors so that a thread
+// loads its element's data with 3 float4 (FP32) or 6 double2 (FP64) loads, coalesced over e.
+__device__ __forceinline__ void load_qp(const float* qpd, int NE, int q, int e, float (&d)[12]) {
+  const float4* b = reinterpret_cast<const float4*>(qpd) + (size_t)(q * 3) * NE + e;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float4 v = b[(size_t)j * NE];
+    d[4 * j] = v.x;
+    d[4 * j + 1] = v.y;
+    d[4 * j + 2] = v.z;
+    d[4 * j + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_qp(const double* qpd, int NE, int q, int e, double (&d)[12]) {
+  const double2* b = reinterpret_cast<const double2*>(qpd) + (size_t)(q * 6) * NE + e;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const double2 v = b[(size_t)j * NE];
+    d[2 * j] = v.x;
+    d[2 * j + 1] = v.y;
+  }
+}
+__device__ __forceinline__ void store_qp(float* qpd, int NE, int q, int e, const float (&d)[12]) {
+  float4* b = reinterpret_cast<float4*>(qpd) + (size_t)(q * 3) * NE + e;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) b[(size_t)j * NE] = make_float4(d[4 * j], d[4 * j + 1], d[4 * j + 2], d[4 * j + 3]);
+}
+__device__ __forceinline__ void store_qp(double* qpd, int NE, int q, int e, const double (&d)[12]) {
+  double2* b = reinterpret_cast<double2*>(qpd) + (size_t)(q * 6) * NE + e;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) b[(size_t)j * NE] = make_double2(d[2 * j], d[2 * j + 1]);
+}
 
 __device__ __forceinline__ double g01(int g) { return g == 0 ? 0.21132486540518711775 : 0.78867513459481288225; }
 
@@ -158,7 +191,7 @@ template <typename TA>
 struct Scratch3 {
   // per-block global scratch, layout set by scratch3_layout
   double* Rf;   // [24][NE] element forces (FP64)
-  TA* qpd;      // [kQp3][8][NE] Gauss-point material data
+  TA* qpd;      // [8][kQp3][NE] Gauss-point material data (4-wide groups, see load_qp)
   TA* x;        // [3][NN] PCG solution
   TA* r;        // [3][NN]
   TA* p;        // [3][NN]
@@ -316,11 +349,13 @@ __device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double
 #pragma unroll
       for (int k = 0; k < 9; ++k) F[k] = (TA)c.Fb[k] + ih * G[k];
       const NH3<TA> m = nh3_eval(F, lam, mu);
-      TA* qd = c.sc.qpd + (size_t)q * c.NE + e;
+      TA qv[12];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) qd[(size_t)k * 8 * c.NE] = m.Fit[k];
-      qd[(size_t)9 * 8 * c.NE] = m.hb;
-      qd[(size_t)10 * 8 * c.NE] = m.gm;
+      for (int k = 0; k < 9; ++k) qv[k] = m.Fit[k];
+      qv[9] = m.hb;
+      qv[10] = m.gm;
+      qv[11] = TA(0);
+      store_qp(c.sc.qpd, c.NE, q, e, qv);
       // diagonal blocks: K_aa,ik = wq [mu |g_a|^2 d_ik + (gm - hb) v_a,i v_a,k], v_a = Fit g_a
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
@@ -399,8 +434,8 @@ __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
     TA y[8][3];
 #pragma unroll
     for (int a = 0; a < 8; ++a) y[a][0] = y[a][1] = y[a][2] = TA(0);
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {  // fully unrolled: the shape-function weights fold to constants
       const TA s = (TA)g01(q & 1), t = (TA)g01((q >> 1) & 1), r = (TA)g01(q >> 2);
       TA dF[9];
       if (mode == 0) {
@@ -412,13 +447,10 @@ __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) dF[k] = k == cidx ? TA(1) : TA(0);
       }
-      const TA* qd = c.sc.qpd + (size_t)q * c.NE + e;
-      TA Fit[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Fit[k] = qd[(size_t)k * 8 * c.NE];
-      const TA hb = qd[(size_t)9 * 8 * c.NE], gm = qd[(size_t)10 * 8 * c.NE];
+      TA qv[12];
+      load_qp(c.sc.qpd, c.NE, q, e, qv);
       TA dP[9];
-      tangent_action(Fit, hb, gm, mu, dF, dP);
+      tangent_action(qv, qv[9], qv[10], mu, dF, dP);
       nat_scatter(dP, cw, s, t, r, y);
     }
 #pragma unroll
