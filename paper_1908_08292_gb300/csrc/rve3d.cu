@@ -302,6 +302,39 @@ __device__ __noinline__ void residual3(const Ctx3<TA>& c, const double* w, doubl
   }
 }
 
+// sum over this thread's elements of psi at the Gauss points (FP64; Eq. NH-free-energy)
+template <typename TA>
+__device__ __noinline__ double energy3(const Ctx3<TA>& c, const double* w) {
+  const int n = c.g.n;
+  const double ih = (double)n;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < c.NE; e += blockDim.x) {
+    int nd[8];
+    c.g.corners(e, nd);
+    double u[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = w[3 * nd[a] + i];
+    const int ph = c.phase[e];
+    const double lam = c.lame[2 * ph], mu = c.lame[2 * ph + 1];
+    for (int q = 0; q < 8; ++q) {
+      const double s = g01(q & 1), t = g01((q >> 1) & 1), r = g01(q >> 2);
+      double G[9], F[9];
+      nat_grad(u, s, t, r, G);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) F[k] = c.Fb[k] + ih * G[k];
+      const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                       F[2] * (F[3] * F[7] - F[4] * F[6]);
+      double trC = 0.0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) trC += F[k] * F[k];
+      acc += 0.25 * lam * (J * J - 1.0) - (0.5 * lam + mu) * log(J) + 0.5 * mu * (trC - 3.0);
+    }
+  }
+  return acc;
+}
+
 // gather element forces of node v: corner a of element (node - offset(a))
 template <typename TA>
 __device__ __forceinline__ void gather_R(const Ctx3<TA>& c, int v, double (&R)[3]) {
@@ -649,7 +682,8 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
   double Pv[10];
 #pragma unroll
   for (int k = 0; k < 9; ++k) Pv[k] = Psum[k];
-  Pv[9] = 0.0;
+  const bool want_W = usable && (a.flags & kFlagEnergy) && a.W != nullptr;
+  Pv[9] = want_W ? energy3(c, w) : 0.0;
   block_sum_n<double>(Pv, 10, c.red);
   if (threadIdx.x == 0)
     for (int k = 0; k < 10; ++k) misc[k] = Pv[k];
@@ -713,6 +747,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
     if (usable) {
       const double wq = 0.125 / ((double)n * n * n);
       for (int k = 0; k < 9; ++k) a.P[(size_t)qp * 9 + k] = misc[k] * wq;
+      if (want_W) a.W[qp] = misc[9] * wq;
     }
   }
   __syncthreads();

@@ -51,10 +51,12 @@ def test_config3_generator_rves(precision):
     p = synth.config3(macro=1, sizes=(8,), n_rve=3)
     Fs = np.array([np.diag([1.0 + s, 1.0 - 0.3 * s, 1.0 - 0.3 * s]) for s in (0.02, 0.1, 0.2)])
     opts = STRICT if precision == "fp64" else {}
-    out = gpu_batch(3, precision, p.rve_n, p.rve_phase, p.rve_E, p.rve_nu, np.arange(3), Fs, **opts)
+    out = gpu_batch(3, precision, p.rve_n, p.rve_phase, p.rve_E, p.rve_nu, np.arange(3), Fs, flags=4, **opts)
     refs = [PeriodicRVE(8, 3, p.rve_phase[r], p.rve_E[r], p.rve_nu[r]).solve(Fs[r], rtol=1e-14, atol=1e-16)
             for r in range(3)]
     check(out, refs, TOL[precision])
+    for q in range(3):  # homogenised energy <psi>
+        assert abs(out["W"][q] - refs[q]["W"]) <= TOL[precision] * abs(refs[q]["W"])
 
 
 def test_homogeneous_rve_is_pointwise_law_3d():

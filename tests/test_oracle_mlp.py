@@ -1,0 +1,63 @@
+"""Pins of the FP64 surrogate-MLP oracle by central finite differences: dy/dx, the input
+Hessian, and the parameter gradient of the Sobolev loss (value + input-gradient targets)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp
+
+
+@pytest.fixture(scope="module")
+def net():
+    p = mlp.init_params(7, width=16)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = 0.1 * synth.random_field(8, 1, p[k].size, 1.0)[0]
+    return p
+
+
+def _small(monkeypatch):
+    monkeypatch.setattr(mlp, "WIDTH", 16)
+
+
+def test_input_grad_and_hessian_fd(net, monkeypatch):
+    _small(monkeypatch)
+    x = synth.random_field(9, 3, 6, 0.8)
+    y, g, H = mlp.input_hessian(net, x)
+    h = 1e-5
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        yp, gp, _, _ = mlp.input_grad(net, x + e)
+        ym, gm, _, _ = mlp.input_grad(net, x - e)
+        np.testing.assert_allclose((yp - ym) / (2 * h), g[:, k], atol=1e-8)
+        np.testing.assert_allclose((gp - gm) / (2 * h), H[:, :, k], atol=1e-7)
+    np.testing.assert_allclose(H, np.swapaxes(H, 1, 2), atol=1e-10)  # symmetric
+
+
+def test_param_grad_fd(net, monkeypatch):
+    _small(monkeypatch)
+    x = synth.random_field(10, 4, 6, 0.8)
+    ty = synth.random_field(11, 1, 4, 1.0)[0]
+    tg = synth.random_field(12, 4, 6, 1.0)
+    G = mlp.param_grad(net, x, ty, tg, 0.7, 1.3)
+    h = 1e-6
+    rng_idx = synth.uniform(13, np.arange(len(net)), 3)
+    for j, (name, v) in enumerate(net.items()):
+        for u in rng_idx[j]:
+            i = int(u * v.size)
+            pp = {k: a.copy() for k, a in net.items()}
+            pm = {k: a.copy() for k, a in net.items()}
+            pp[name].reshape(-1)[i] += h
+            pm[name].reshape(-1)[i] -= h
+            fd = (mlp.loss(pp, x, ty, tg, 0.7, 1.3) - mlp.loss(pm, x, ty, tg, 0.7, 1.3)) / (2 * h)
+            assert abs(fd - G[name].reshape(-1)[i]) < 1e-6 * max(1.0, abs(fd)), (name, i, fd, G[name].reshape(-1)[i])
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    # 1 + 2^-8 lies halfway between bf16 neighbours 1 and 1 + 2^-7: ties go to the even (1.0)
+    v = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5, 3.0e-3])
+    r = mlp.to_bf16(v)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2.0 ** -6
+    assert r[3] == -2.5
+    assert abs(r[4] - 3.0e-3) <= 3.0e-3 * 2.0 ** -8
