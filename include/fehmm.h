@@ -138,6 +138,20 @@ int fehmm_bind_qps(fehmm_ctx* ctx, int n_qp, const int32_t* rve_of_qp);
 int fehmm_rve_solve(fehmm_ctx* ctx, const double* F, double* P, double* A, double* W,
                     int32_t* status, int32_t* iters, int flags, void* stream);
 
+/*
+ * Same as fehmm_rve_solve for the quadrature points list[0 .. *count-1] only (device arrays;
+ * *count is read on the device, so the list can come from fehmm_select without a host
+ * round trip).  Outputs of the other points are left unchanged.  Used for the fallback of the
+ * surrogate path and for its audit sample.
+ */
+int fehmm_rve_solve_list(fehmm_ctx* ctx, const double* F, double* P, double* A, double* W,
+                         int32_t* status, int32_t* iters, int flags, const int32_t* list,
+                         const int32_t* count, void* stream);
+
+/* list <- indices q (ascending) with mask[q] == value, *count <- their number (device arrays,
+ * list of n entries). */
+int fehmm_select(const int32_t* mask, int n, int value, int32_t* list, int32_t* count, void* stream);
+
 /* Load-step state: commit copies current -> committed fluctuations; rollback the reverse. */
 int fehmm_commit(fehmm_ctx* ctx, void* stream);
 int fehmm_rollback(fehmm_ctx* ctx, void* stream);
@@ -199,6 +213,57 @@ int fehmm_macro_solve(fehmm_ctx* ctx, const double* K_vals, const double* f, dou
 /* CSR pattern of the macro tangent (device pointers owned by the context). */
 int fehmm_macro_csr(fehmm_ctx* ctx, const int32_t** rowptr, const int32_t** col, int* n_rows,
                     int* nnz);
+
+/*
+ * Energy surrogate (the learned part of the workload; the paper has no counterpart).
+ * An MLP y(x), x in R^6 -> 4 x 128 SiLU -> 1, with BF16 weights and activations and FP32
+ * accumulation on tensor cores.  Parameters are packed FP32 (fehmm_mlp_num_params floats):
+ * W1 [128][8] (input columns 6, 7 unused), b1 [128], W2, W3, W4 [128][128] row-major
+ * ([out][in]), b2..b4 [128], w5 [128], b5 [1], padding [3].  The context holds FP32 master
+ * weights, BF16 copies, AdamW moments and a workspace for up to max_batch samples.
+ */
+typedef struct fehmm_mlp fehmm_mlp;
+int fehmm_mlp_num_params(void);
+int fehmm_mlp_create(fehmm_mlp** out, int max_batch);
+int fehmm_mlp_destroy(fehmm_mlp* mlp);
+/* host_params: packed FP32 parameters (copied); resets the optimiser state. */
+int fehmm_mlp_set_params(fehmm_mlp* mlp, const float* host_params);
+/* host copies of the parameters and/or of the last computed gradient (either may be NULL). */
+int fehmm_mlp_get_params(fehmm_mlp* mlp, float* host_params, float* host_grad);
+/* y [B], g = dy/dx [B][6], H = d2y/dx2 [B][6][6] (device; g, H may be NULL) for x [B][6]. */
+int fehmm_mlp_eval(fehmm_mlp* mlp, const float* x, int B, float* y, float* g, float* H, void* stream);
+/* Training loss L = 1/2 sum_b [cy (y_b - ty_b)^2 + cg |g_b - tg_b|^2] (device x [B][6],
+ * ty [B], tg [B][6]); writes L to loss (device float, may be NULL) and its exact gradient
+ * with respect to the parameters to the context (read with fehmm_mlp_get_params). */
+int fehmm_mlp_loss_grad(fehmm_mlp* mlp, const float* x, const float* ty, const float* tg, int B, float cy,
+                        float cg, float* loss, void* stream);
+/* AdamW step on the FP32 masters with the last gradient (weight decay on weights only). */
+int fehmm_mlp_adamw(fehmm_mlp* mlp, float lr, float beta1, float beta2, float eps, float weight_decay,
+                    void* stream);
+long long fehmm_mlp_launch_count(const fehmm_mlp* mlp);
+
+typedef struct {
+  double lam0, mu0;  /* Lame constants of the neo-Hookean base energy */
+  double sx, sg;     /* input scale (x = Mandel(E)/sx) and output scale (W = W_base + sg y) */
+  double radius;     /* trust region |U - I|_F <= radius, U = (F^T F)^(1/2) */
+} fehmm_surrogate_params;
+
+/*
+ * Surrogate constitutive evaluation at n macro points: F device [n][9] in; P [n][9],
+ * A [n][81] (may be NULL), W [n] (may be NULL), inside [n] (1 inside the trust region,
+ * else 0) out; work: device floats, fehmm_surrogate_work_floats(n) of them; n <= the MLP's
+ * max_batch.  P and A are written for every point; the caller replaces the points outside
+ * the trust region by full RVE solves (fehmm_select + fehmm_rve_solve_list).
+ */
+int fehmm_surrogate_eval(fehmm_mlp* mlp, const fehmm_surrogate_params* sp, const double* F, int n,
+                         double* P, double* A, double* W, int32_t* inside, float* work, void* stream);
+size_t fehmm_surrogate_work_floats(int n);
+
+/* Training data of the surrogate from n full RVE solves at F = U (device F [n][9], their
+ * homogenised P [n][9] and W [n]): features x [n][6], value targets ty [n] and input-gradient
+ * targets tg [n][6] (device floats) of the Sobolev loss of fehmm_mlp_loss_grad. */
+int fehmm_surrogate_targets(const fehmm_surrogate_params* sp, const double* F, const double* P, const double* W,
+                            int n, float* x, float* ty, float* tg, void* stream);
 
 /* Number of kernel launches this context has issued since creation (for accounting). */
 long long fehmm_launch_count(const fehmm_ctx* ctx);

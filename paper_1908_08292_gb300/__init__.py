@@ -61,6 +61,20 @@ _SIGS = {
     "fehmm_macro_csr": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fehmm_launch_count": (ctypes.c_longlong, [_P]),
     "fehmm_status_str": (ctypes.c_char_p, [_I]),
+    "fehmm_rve_solve_list": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P]),
+    "fehmm_select": (_I, [_P, _I, _I, _P, _P, _P]),
+    "fehmm_mlp_num_params": (_I, []),
+    "fehmm_mlp_create": (_I, [ctypes.POINTER(_P), _I]),
+    "fehmm_mlp_destroy": (_I, [_P]),
+    "fehmm_mlp_set_params": (_I, [_P, _P]),
+    "fehmm_mlp_get_params": (_I, [_P, _P, _P]),
+    "fehmm_mlp_eval": (_I, [_P, _P, _I, _P, _P, _P, _P]),
+    "fehmm_mlp_loss_grad": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, ctypes.c_float, _P, _P]),
+    "fehmm_mlp_adamw": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "fehmm_mlp_launch_count": (ctypes.c_longlong, [_P]),
+    "fehmm_surrogate_eval": (_I, [_P, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
+    "fehmm_surrogate_work_floats": (ctypes.c_size_t, [_I]),
+    "fehmm_surrogate_targets": (_I, [_P, _P, _P, _P, _I, _P, _P, _P, _P]),
     "fehmm_rve2d_solve_fp64_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options), _P]),
 }
 
@@ -109,6 +123,14 @@ def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def select(mask, value, out_list, out_count, stream=None):
+    """out_list[:out_count[0]] <- indices with mask == value (device, ascending)."""
+    import torch
+    _check(lib().fehmm_select(_dev(mask, torch.int32, "mask"), int(mask.numel()), int(value),
+                              _dev(out_list, torch.int32, "list", mask.numel()), _dev(out_count, torch.int32, "count", 1),
+                              _stream(stream)), "select")
 
 
 class _DevArray:
@@ -198,6 +220,17 @@ class Context:
                                      _dev(status, torch.int32, "status", n),
                                      _dev(iters, torch.int32, "iters", 4 * n), int(flags), _stream(stream)),
                "rve_solve")
+
+    def rve_solve_list(self, F, P, A, status, iters, flags, qp_list, count, W=None, stream=None):
+        """RVE solves for the quadrature points qp_list[:count[0]] (device int32 arrays)."""
+        import torch
+        d, n = self.dim, self.n_qp
+        _check(lib().fehmm_rve_solve_list(self._h, _dev(F, torch.float64, "F", n * d * d),
+                                          _dev(P, torch.float64, "P", n * d * d), _dev(A, torch.float64, "A"),
+                                          _dev(W, torch.float64, "W"), _dev(status, torch.int32, "status", n),
+                                          _dev(iters, torch.int32, "iters"), int(flags),
+                                          _dev(qp_list, torch.int32, "qp_list"), _dev(count, torch.int32, "count", 1),
+                                          _stream(stream)), "rve_solve_list")
 
     def commit(self, stream=None):
         _check(lib().fehmm_commit(self._h, _stream(stream)), "commit")

@@ -266,8 +266,22 @@ int fehmm_bind_qps(fehmm_ctx* c, int n_qp, const int32_t* rve_of_qp) {
   return FEHMM_OK;
 }
 
+static int rve_solve_impl(fehmm_ctx* c, const double* F, double* P, double* A, double* W, int32_t* status,
+                          int32_t* iters, int flags, const int32_t* list, const int32_t* count, void* stream);
+
 int fehmm_rve_solve(fehmm_ctx* c, const double* F, double* P, double* A, double* W, int32_t* status, int32_t* iters,
                     int flags, void* stream) {
+  return rve_solve_impl(c, F, P, A, W, status, iters, flags, nullptr, nullptr, stream);
+}
+
+int fehmm_rve_solve_list(fehmm_ctx* c, const double* F, double* P, double* A, double* W, int32_t* status,
+                         int32_t* iters, int flags, const int32_t* list, const int32_t* count, void* stream) {
+  if (!list || !count) return FEHMM_ERR_ARG;
+  return rve_solve_impl(c, F, P, A, W, status, iters, flags, list, count, stream);
+}
+
+static int rve_solve_impl(fehmm_ctx* c, const double* F, double* P, double* A, double* W, int32_t* status,
+                          int32_t* iters, int flags, const int32_t* list, const int32_t* count, void* stream) {
   if (!c || !F || !P || !status) return FEHMM_ERR_ARG;
   if (!(flags & FEHMM_SOLVE_NO_TANGENT) && !A) return FEHMM_ERR_ARG;
   if ((flags & FEHMM_SOLVE_ENERGY) && !W) return FEHMM_ERR_ARG;
@@ -276,7 +290,8 @@ int fehmm_rve_solve(fehmm_ctx* c, const double* F, double* P, double* A, double*
   Rve2dArgs a{};
   a.n_qp = c->n_qp;
   a.nn_max = c->nn_max;
-  a.order = c->d_order;
+  a.order = list ? list : c->d_order;
+  a.n_dev = count;
   a.qp_rve = c->d_qp_rve;
   a.rve_n = c->d_rve_n;
   a.rve_phase_off = c->d_rve_phase_off;

@@ -918,7 +918,7 @@ __global__ void __launch_bounds__(kThreads2D, 1) rve2d_kernel(const Rve2dArgs a)
     __syncthreads();
     const int item = s_item;
     __syncthreads();
-    if (item >= a.n_qp) break;
+    if (item >= (a.n_dev ? *a.n_dev : a.n_qp)) break;
     solve_item_2d<TA, kFixed>(a, kFixed ? item : a.order[item], sm, gscr);
   }
 }

@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(kThreads3D, 1) rve3d_kernel(const Rve2dArgs a)
     __syncthreads();
     const int item = s_item;
     __syncthreads();
-    if (item >= a.n_qp) break;
+    if (item >= (a.n_dev ? *a.n_dev : a.n_qp)) break;
     solve_item_3d<TA>(a, a.order[item], smem3, gscr);
   }
 }

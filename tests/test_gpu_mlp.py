@@ -1,0 +1,147 @@
+"""GPU parity of the BF16 tensor-core MLP and the surrogate evaluation with the FP64 oracles.
+
+The oracle rounds the weights and every matrix-product operand to bfloat16 at the same points as
+the kernels (oracle.mlp, bf16=True); what remains is FP32 accumulation order and the FP32 vs FP64
+evaluation of silu before rounding, so the tolerances are a few bfloat16 units (2^-8) relative."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+from oracle import surrogate as osur
+
+pytestmark = pytest.mark.gpu
+
+
+def net(seed):
+    p = omlp.init_params(seed)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = 0.1 * synth.random_field(seed + 1, 1, p[k].size, 1.0)[0]
+    return p
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_mlp_eval_forward_gradient_hessian():
+    import torch
+
+    from paper_1908_08292_gb300.surrogate import MLP
+    p = net(41)
+    B = 300  # ragged: not a multiple of the 64-row tile
+    x = synth.random_field(43, B, 6, 0.9)
+    dev = torch.device("cuda:0")
+    m = MLP(512)
+    m.set_params(p)
+    xt = torch.tensor(x, dtype=torch.float32, device=dev)
+    y = torch.zeros(B, dtype=torch.float32, device=dev)
+    g = torch.zeros(B, 6, dtype=torch.float32, device=dev)
+    H = torch.zeros(B, 6, 6, dtype=torch.float32, device=dev)
+    m.eval(xt, y, g, H)
+    torch.cuda.synchronize()
+    yr, gr, Hr = omlp.input_hessian(p, x, bf16=True)
+    assert rel(y.cpu().numpy(), yr) < 4e-3
+    assert rel(g.cpu().numpy(), gr) < 4e-3
+    assert rel(H.cpu().numpy(), Hr) < 8e-3
+    # and close to the unquantised FP64 network (BF16 error budget)
+    y64, g64, H64 = omlp.input_hessian(p, x)
+    assert rel(y.cpu().numpy(), y64) < 3e-2 and rel(g.cpu().numpy(), g64) < 3e-2
+    m.close()
+
+
+def test_mlp_loss_parameter_gradient():
+    import torch
+
+    from paper_1908_08292_gb300.surrogate import MLP, unpack
+    p = net(51)
+    B = 257
+    x = synth.random_field(52, B, 6, 0.9)
+    ty = synth.random_field(53, 1, B, 1.0)[0]
+    tg = synth.random_field(54, B, 6, 1.0)
+    cy, cg = 0.7, 1.3
+    dev = torch.device("cuda:0")
+    m = MLP(512)
+    m.set_params(p)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    m.loss_grad(torch.tensor(x, dtype=torch.float32, device=dev), torch.tensor(ty, dtype=torch.float32, device=dev),
+                torch.tensor(tg, dtype=torch.float32, device=dev), cy, cg, loss)
+    torch.cuda.synchronize()
+    G = unpack(m.get_grad())
+    Gr = omlp.param_grad(p, x, ty, tg, cy, cg, bf16=True)
+    Lr = omlp.loss(p, x, ty, tg, cy, cg, bf16=True)
+    assert abs(loss.item() - Lr) < 2e-3 * Lr
+    for k in Gr:
+        assert rel(G[k], Gr[k]) < 2e-2, (k, rel(G[k], Gr[k]))
+    m.close()
+
+
+def test_surrogate_eval_and_trust_region():
+    import torch
+
+    from paper_1908_08292_gb300.surrogate import MLP, SurrogateParams, surrogate_eval, work_floats
+    p = net(61)
+    n = 200
+    F = synth.random_F(62, n, 3, 0.25)
+    lam0, mu0, sx, sg, radius = 1.5, 0.9, 0.35, 0.02, 0.3
+    dev = torch.device("cuda:0")
+    m = MLP(n)
+    m.set_params(p)
+    sp = SurrogateParams(lam0, mu0, sx, sg, radius)
+    Ft = torch.tensor(F.reshape(n, 9), device=dev)
+    P = torch.zeros(n, 9, dtype=torch.float64, device=dev)
+    A = torch.zeros(n, 81, dtype=torch.float64, device=dev)
+    W = torch.zeros(n, dtype=torch.float64, device=dev)
+    inside = torch.zeros(n, dtype=torch.int32, device=dev)
+    work = torch.zeros(work_floats(n), dtype=torch.float32, device=dev)
+    surrogate_eval(m, sp, Ft, P, A, W, inside, work)
+    torch.cuda.synchronize()
+    Wr, Pr, Ar = osur.evaluate(p, F, lam0, mu0, sx, sg, bf16=True)
+    d = osur.stretch_distance(F)
+    ins = inside.cpu().numpy()
+    clear = np.abs(d - radius) > 1e-9
+    assert np.array_equal(ins[clear], (d[clear] <= radius).astype(np.int32)[clear])
+    assert 0 < ins.sum() < n  # both sides of the trust boundary are exercised
+    # the base law is evaluated in FP64 on both sides; the network part (sg y and its derivatives)
+    # carries the bfloat16 budget: a few 2^-8 units relative to its own size
+    from oracle import material as mat
+    Wb, Pb, Ab = mat.psi(F, lam0, mu0), mat.P_of_F(F, lam0, mu0), mat.A_of_F(F, lam0, mu0)
+    assert np.linalg.norm(W.cpu().numpy() - Wr) < 8e-3 * np.linalg.norm(Wr - Wb)
+    assert np.linalg.norm(P.cpu().numpy() - Pr.reshape(n, 9)) < 8e-3 * np.linalg.norm((Pr - Pb).reshape(n, 9))
+    assert np.linalg.norm(A.cpu().numpy() - Ar.reshape(n, 81)) < 1.6e-2 * np.linalg.norm((Ar - Ab).reshape(n, 81))
+    # with a zero network the surrogate is exactly the base law
+    m.set_params(np.zeros_like(m.get_params()))
+    surrogate_eval(m, sp, Ft, P, A, W, inside, work)
+    torch.cuda.synchronize()
+    assert rel(W.cpu().numpy(), Wb) < 1e-13
+    assert rel(P.cpu().numpy(), Pb.reshape(n, 9)) < 1e-13
+    assert rel(A.cpu().numpy(), Ab.reshape(n, 81)) < 1e-13
+    m.close()
+
+
+def test_training_reduces_sobolev_loss():
+    """A student network trained with the library's loss/gradient/AdamW kernels fits a teacher
+    network's values and input gradients (Sobolev loss) far better than at initialisation."""
+    import torch
+
+    from paper_1908_08292_gb300.surrogate import MLP, init_params
+    teacher = net(71)
+    B = 1024
+    x = synth.random_field(72, B, 6, 0.9)
+    ty, tg, _ = omlp.input_grad(teacher, x)[:2] + (None,)
+    dev = torch.device("cuda:0")
+    xt = torch.tensor(x, dtype=torch.float32, device=dev)
+    tyt = torch.tensor(ty, dtype=torch.float32, device=dev)
+    tgt = torch.tensor(tg, dtype=torch.float32, device=dev)
+    m = MLP(B)
+    m.set_params(init_params(73))
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    hist = []
+    for it in range(300):
+        m.loss_grad(xt, tyt, tgt, 1.0 / B, 1.0 / B, loss)
+        m.adamw(2e-3)
+        if it % 50 == 0 or it == 299:
+            hist.append(loss.item())
+    assert hist[-1] < 0.05 * hist[0], hist
+    m.close()

@@ -61,3 +61,32 @@ def test_bf16_rounding_is_round_to_nearest_even():
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2.0 ** -6
     assert r[3] == -2.5
     assert abs(r[4] - 3.0e-3) <= 3.0e-3 * 2.0 ** -8
+
+
+def test_surrogate_chain_rule_fd():
+    from oracle import surrogate as sur
+    p = mlp.init_params(21)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = 0.05 * synth.random_field(22, 1, p[k].size, 1.0)[0]
+    F = synth.random_F(23, 2, 3, 0.12)
+    lam0, mu0, sx, sg = 1.2, 0.8, 0.35, 0.05
+    W, P, A = sur.evaluate(p, F, lam0, mu0, sx, sg)
+    h = 1e-6
+    for k in range(3):
+        for l in range(3):
+            E = np.zeros((3, 3))
+            E[k, l] = h
+            Wp, Pp, _ = sur.evaluate(p, F + E, lam0, mu0, sx, sg)
+            Wm, Pm, _ = sur.evaluate(p, F - E, lam0, mu0, sx, sg)
+            np.testing.assert_allclose((Wp - Wm) / (2 * h), P[:, k, l], atol=2e-8)
+            np.testing.assert_allclose((Pp - Pm) / (2 * h), A[:, :, :, k, l], atol=2e-7)
+
+
+def test_stretch_distance_closed_form():
+    from oracle import surrogate as sur
+    U = synth.stretch_ball(31, 5, 0.3)
+    R = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    d = sur.stretch_distance(R @ U)  # rotation-invariant: |U - I|_F of the stretch
+    np.testing.assert_allclose(d, np.linalg.norm(U - np.eye(3), axis=(1, 2)), atol=1e-12)
+    assert np.all(d <= 0.3 + 1e-12)
