@@ -148,9 +148,10 @@ int fehmm_rve_solve_list(fehmm_ctx* ctx, const double* F, double* P, double* A, 
                          int32_t* status, int32_t* iters, int flags, const int32_t* list,
                          const int32_t* count, void* stream);
 
-/* list <- indices q (ascending) with mask[q] == value, *count <- their number (device arrays,
- * list of n entries). */
-int fehmm_select(const int32_t* mask, int n, int value, int32_t* list, int32_t* count, void* stream);
+/* list <- indices q (ascending) with mask[q] == value and q % stride == 0, *count <- their
+ * number (device arrays, list of n entries; stride >= 1, e.g. > 1 for an audit sample). */
+int fehmm_select(const int32_t* mask, int n, int value, int stride, int32_t* list, int32_t* count,
+                 void* stream);
 
 /* Load-step state: commit copies current -> committed fluctuations; rollback the reverse. */
 int fehmm_commit(fehmm_ctx* ctx, void* stream);
@@ -246,6 +247,11 @@ typedef struct {
   double lam0, mu0;  /* Lame constants of the neo-Hookean base energy */
   double sx, sg;     /* input scale (x = Mandel(E)/sx) and output scale (W = W_base + sg y) */
   double radius;     /* trust region |U - I|_F <= radius, U = (F^T F)^(1/2) */
+  double Ca[36];     /* anisotropic small-strain part of the base energy, 1/2 m(E).Ca.m(E) with
+                        m(E) the Mandel vector of E (order 11,22,33,23,13,12, sqrt 2 on shears) */
+  double y0, g0[6], H0[36]; /* network value, gradient and Hessian at x = 0, subtracted so that the
+                        learned correction y(x) - y0 - g0.x - 1/2 x.H0.x vanishes to third order at
+                        E = 0, where the base energy is exact to second order (zeros: no shift) */
 } fehmm_surrogate_params;
 
 /*

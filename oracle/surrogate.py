@@ -50,17 +50,32 @@ def _to_tensor4(H):
     return CC
 
 
-def evaluate(params, F, lam0, mu0, sx, sg, bf16=False):
-    """W, P, A at deformation gradients F (..., 3, 3)."""
+def evaluate(params, F, lam0, mu0, sx, sg, bf16=False, Ca=None, origin=None):
+    """W, P, A at deformation gradients F (..., 3, 3).  Ca (6x6 Mandel, optional): anisotropic
+    quadratic base term 1/2 m(E).Ca.m(E), m(E) the Mandel vector of E.  origin = (y0, g0, H0)
+    (optional): the network's Taylor terms at x = 0, subtracted from the correction."""
     F = np.asarray(F, dtype=np.float64)
     x = features(F, sx).reshape(-1, 6)
     y, g, H = mlp.input_hessian(params, x, bf16)
     shp = F.shape[:-2]
     y, g, H = y.reshape(shp), g.reshape(shp + (6,)), H.reshape(shp + (6, 6))
+    if origin is not None:
+        y0, g0, H0 = (np.asarray(v, dtype=np.float64) for v in origin)
+        xs = x.reshape(shp + (6,))
+        hx = xs @ H0.T
+        y = y - y0 - (xs * g0).sum(-1) - 0.5 * (xs * hx).sum(-1)
+        g = g - g0 - hx
+        H = H - H0
     C = np.swapaxes(F, -1, -2) @ F
     Wb = mat.psi(F, lam0, mu0)
     S = mat.S_of_C(C, lam0, mu0) + sg / sx * _to_tensor2(g)
     CC = mat.CC_of_C(C, lam0, mu0) + sg / sx ** 2 * _to_tensor4(H)
+    if Ca is not None:
+        m = features(F, 1.0)  # Mandel vector of E
+        sm = m @ np.asarray(Ca).T
+        Wb = Wb + 0.5 * (m * sm).sum(-1)
+        S = S + _to_tensor2(sm)
+        CC = CC + _to_tensor4(np.broadcast_to(np.asarray(Ca), sm.shape[:-1] + (6, 6)))
     P = F @ S
     A = np.einsum("ik,...JL->...iJkL", np.eye(3), S) + np.einsum("...iI,...kK,...IJKL->...iJkL", F, F, CC)
     return Wb + sg * y, P, A

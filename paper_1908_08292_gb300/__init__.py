@@ -62,7 +62,7 @@ _SIGS = {
     "fehmm_launch_count": (ctypes.c_longlong, [_P]),
     "fehmm_status_str": (ctypes.c_char_p, [_I]),
     "fehmm_rve_solve_list": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P]),
-    "fehmm_select": (_I, [_P, _I, _I, _P, _P, _P]),
+    "fehmm_select": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "fehmm_mlp_num_params": (_I, []),
     "fehmm_mlp_create": (_I, [ctypes.POINTER(_P), _I]),
     "fehmm_mlp_destroy": (_I, [_P]),
@@ -125,10 +125,10 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def select(mask, value, out_list, out_count, stream=None):
-    """out_list[:out_count[0]] <- indices with mask == value (device, ascending)."""
+def select(mask, value, out_list, out_count, stride=1, stream=None):
+    """out_list[:out_count[0]] <- indices q with mask == value and q % stride == 0 (device, ascending)."""
     import torch
-    _check(lib().fehmm_select(_dev(mask, torch.int32, "mask"), int(mask.numel()), int(value),
+    _check(lib().fehmm_select(_dev(mask, torch.int32, "mask"), int(mask.numel()), int(value), int(stride),
                               _dev(out_list, torch.int32, "list", mask.numel()), _dev(out_count, torch.int32, "count", 1),
                               _stream(stream)), "select")
 

@@ -22,6 +22,9 @@ constexpr int kStatusOk = 0, kStatusNewtonCap = 1, kStatusJNonPos = 2, kStatusPc
               kStatusNonFinite = 4, kStatusPcgCap = 5,
               kStatusNegCurv = 6;  // internal: truncated Newton-correction PCG
 constexpr int kFlagNoTangent = 1, kFlagFromCommitted = 2, kFlagEnergy = 4;
+// Newton globalisation: after an update that makes det F <= 0 somewhere (or the residual
+// non-finite) the step is halved, up to this many times, before the RVE is reported failed.
+constexpr int kMaxStepHalvings = 8;
 
 template <typename T> struct vec2_of;
 template <> struct vec2_of<float> { using type = float2; };

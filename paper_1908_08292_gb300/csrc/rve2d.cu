@@ -735,8 +735,8 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   vec2_t<TA>* Lb = Xs + 4 * NN;                               // [4][NN]
   TA Minv[2][4];
 
-  int status = kStatusNewtonCap, it = 0, cg_total = 0;
-  double r0 = 0.0;
+  int status = kStatusNewtonCap, it = 0, cg_total = 0, nhalf = 0;
+  double r0 = 0.0, step = 1.0;
   double Psum[4];
   for (;;) {
     // ---- FP64 residual
@@ -767,6 +767,25 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
     block_sum<2, double>(v2, sm.red + (it & 1) * 512);
     const double rn = sqrt(v2[0]);
     if (it == 0) r0 = rn;
+    if ((v2[1] > 0.0 || !isfinite(rn)) && it > 0 && nhalf < kMaxStepHalvings) {
+      // backtrack: w = w_prev + step x  ->  w_prev + (step/2) x
+      ++nhalf;
+      step *= 0.5;
+      if (o.active) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const int nd = o.node[s];
+          double2 wv = sm.w[nd];
+          const vec2_t<TA> dx = sm.x[nd];
+          wv.x -= step * (double)dx.x;
+          wv.y -= step * (double)dx.y;
+          sm.w[nd] = wv;
+          if constexpr (REG) sm.w32[nd] = make_float2((float)wv.x, (float)wv.y);
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     if (v2[1] > 0.0) {
       status = kStatusJNonPos;
       break;
@@ -794,6 +813,8 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       status = kStatusPcgBreakdown;
       break;
     }
+    step = 1.0;
+    nhalf = 0;
     if (o.active) {
 #pragma unroll
       for (int s = 0; s < 2; ++s) {

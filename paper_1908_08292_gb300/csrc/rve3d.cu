@@ -623,8 +623,8 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
   for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) w[v] = v < 3 ? 0.0 : w_in[v];
   __syncthreads();
 
-  int status = kStatusNewtonCap, it = 0, cg_total = 0;
-  double r0 = 0.0, Psum[9];
+  int status = kStatusNewtonCap, it = 0, cg_total = 0, nhalf = 0;
+  double r0 = 0.0, step = 1.0, Psum[9];
   for (;;) {
     double bad = 0.0;
 #pragma unroll
@@ -646,6 +646,18 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
     block_sum_n<double>(v2, 2, c.red);
     const double rn = sqrt(v2[0]);
     if (it == 0) r0 = rn;
+    if ((v2[1] > 0.0 || !isfinite(rn)) && it > 0 && nhalf < kMaxStepHalvings) {
+      // backtrack: w = w_prev + step x  ->  w_prev + (step/2) x
+      ++nhalf;
+      step *= 0.5;
+      for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+        if (v == 0) continue;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) w[3 * v + d] -= step * (double)c.sc.x[d * NN + v];
+      }
+      __syncthreads();
+      continue;
+    }
     if (v2[1] > 0.0) {
       status = kStatusJNonPos;
       break;
@@ -669,6 +681,8 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       status = kStatusPcgBreakdown;
       break;
     }
+    step = 1.0;
+    nhalf = 0;
     for (int v = threadIdx.x; v < NN; v += blockDim.x) {
       if (v == 0) continue;
 #pragma unroll

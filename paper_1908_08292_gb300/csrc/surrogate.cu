@@ -5,6 +5,8 @@
 //     eigenvalues l_i of C (closed-form eigenvalues of a symmetric 3x3 matrix, trigonometric
 //     method of O. K. Smith, Comm. ACM 4 (1961) 168);
 //   energy W(E) = W_base(E) + sg * y(x), x = Mandel(E) / sx, y the MLP;
+//   W_base = neo-Hookean(lam0, mu0) + 1/2 m(E).Ca.m(E), m(E) = Mandel(E) (the anisotropic
+//     small-strain remainder of the RVE's homogenised elasticity tensor);
 //   S = dW/dE, CC = d2W/dEdE, P = F S, A_iJkL = d_ik S_JL + F_iI F_kK CC_IJKL.
 // W_base is the compressible neo-Hookean law of the paper's Sec. 6 (Eq. NH-free-energy and the
 // closed forms for S and CC) with effective Lame constants (lam0, mu0); the network learns the
@@ -21,6 +23,27 @@ namespace {
 
 __constant__ int kMandelI[6] = {0, 1, 2, 1, 0, 0};
 __constant__ int kMandelJ[6] = {0, 1, 2, 2, 2, 1};
+
+struct BaseAniso {
+  double Ca[36];
+  double y0, g0[6], H0[36];
+};
+
+// m = Mandel(E), s = Ca m  (base stress contribution in Mandel form), e = 1/2 m.Ca.m
+__device__ __forceinline__ void aniso_base(const BaseAniso& b, const double (&C)[9], double (&sm)[6], double& e) {
+  double m[6];
+  for (int p = 0; p < 6; ++p) {
+    const int I = kMandelI[p], J = kMandelJ[p];
+    m[p] = (I == J ? 1.0 : 1.4142135623730950488) * 0.5 * (C[3 * I + J] - (I == J ? 1.0 : 0.0));
+  }
+  e = 0.0;
+  for (int p = 0; p < 6; ++p) {
+    double t = 0.0;
+    for (int q = 0; q < 6; ++q) t += b.Ca[6 * p + q] * m[q];
+    sm[p] = t;
+    e += 0.5 * m[p] * t;
+  }
+}
 
 __device__ __forceinline__ int mandel_index(int I, int J) {
   if (I == J) return I;
@@ -74,8 +97,8 @@ __global__ void features_kernel(const double* F, int n, double sx, double radius
   }
 }
 
-__global__ void combine_kernel(const double* F, int n, double lam0, double mu0, double sx, double sg, const float* y,
-                               const float* g, const float* H, double* P, double* A, double* Wout) {
+__global__ void combine_kernel(const double* F, int n, double lam0, double mu0, double sx, double sg, const BaseAniso ba,
+                               const float* y, const float* g, const float* H, double* P, double* A, double* Wout) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const double* f = F + (size_t)q * 9;
@@ -90,15 +113,30 @@ __global__ void combine_kernel(const double* F, int n, double lam0, double mu0, 
   double S[9];
   for (int k = 0; k < 9; ++k) S[k] = 0.5 * lam0 * (J2 - 1.0) * Ci[k] + mu0 * ((k % 4 == 0 ? 1.0 : 0.0) - Ci[k]);
   const double sq2 = 1.4142135623730950488;
+  double sa[6], ea;
+  aniso_base(ba, C, sa, ea);
+  // network correction with its Taylor terms at x = 0 removed
+  double xs[6], gs[6], ys;
+  for (int p = 0; p < 6; ++p) {
+    const int I = kMandelI[p], J = kMandelJ[p];
+    xs[p] = (I == J ? 1.0 : sq2) * 0.5 * (C[3 * I + J] - (I == J ? 1.0 : 0.0)) / sx;
+  }
+  ys = (double)y[q] - ba.y0;
+  for (int p = 0; p < 6; ++p) {
+    double hx = 0.0;
+    for (int r = 0; r < 6; ++r) hx += ba.H0[6 * p + r] * xs[r];
+    gs[p] = (double)g[(size_t)q * 6 + p] - ba.g0[p] - hx;
+    ys -= (ba.g0[p] + 0.5 * hx) * xs[p];
+  }
   for (int I = 0; I < 3; ++I)
     for (int J = 0; J < 3; ++J) {
       const int p = mandel_index(I, J);
-      S[3 * I + J] += sg / sx * (double)g[(size_t)q * 6 + p] / (I == J ? 1.0 : sq2);
+      S[3 * I + J] += (sg / sx * gs[p] + sa[p]) / (I == J ? 1.0 : sq2);
     }
   const double Jd = sqrt(J2);
   if (Wout) {
     const double trC = C[0] + C[4] + C[8];
-    Wout[q] = 0.25 * lam0 * (J2 - 1.0) - (0.5 * lam0 + mu0) * log(Jd) + 0.5 * mu0 * (trC - 3.0) + sg * (double)y[q];
+    Wout[q] = 0.25 * lam0 * (J2 - 1.0) - (0.5 * lam0 + mu0) * log(Jd) + 0.5 * mu0 * (trC - 3.0) + ea + sg * ys;
   }
   for (int i = 0; i < 3; ++i)
     for (int J = 0; J < 3; ++J) P[(size_t)q * 9 + 3 * i + J] = f[3 * i] * S[J] + f[3 * i + 1] * S[3 + J] + f[3 * i + 2] * S[6 + J];
@@ -116,7 +154,8 @@ __global__ void combine_kernel(const double* F, int n, double lam0, double mu0, 
                                      gam * Ci[3 * I + Jj] * Ci[3 * K + L];
               const int pp = mandel_index(I, Jj), qq = mandel_index(K, L);
               const double wp = (I == Jj) ? 1.0 : sq2, wq = (K == L) ? 1.0 : sq2;
-              const double cc = cc_base + sg / (sx * sx) * (double)Hq[pp * 6 + qq] / (wp * wq);
+              const double hn = (double)Hq[pp * 6 + qq] - ba.H0[6 * pp + qq];
+              const double cc = cc_base + (sg / (sx * sx) * hn + ba.Ca[6 * pp + qq]) / (wp * wq);
               acc += f[3 * i + I] * f[3 * k + K] * cc;
             }
           A[(size_t)q * 81 + (3 * i + Jj) * 9 + 3 * k + L] = acc;
@@ -127,7 +166,7 @@ __global__ void combine_kernel(const double* F, int n, double lam0, double mu0, 
 // ty = (Wbar - W_base)/sg and input-gradient target tg_p = (sx/sg) w_p (Sbar - S_base)_p with
 // Sbar = sym(F^-1 Pbar).
 __global__ void targets_kernel(const double* F, const double* Pbar, const double* Wbar, int n, double lam0, double mu0,
-                               double sx, double sg, float* x, float* ty, float* tg) {
+                               double sx, double sg, const BaseAniso ba, float* x, float* ty, float* tg) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const double* f = F + (size_t)q * 9;
@@ -148,12 +187,16 @@ __global__ void targets_kernel(const double* F, const double* Pbar, const double
   const double k11 = C[0] * C[8] - C[2] * C[6], k12 = C[2] * C[3] - C[0] * C[5], k22 = C[0] * C[4] - C[1] * C[3];
   const double J2 = C[0] * k00 + C[1] * k01 + C[2] * k02;
   const double Ci[9] = {k00 / J2, k01 / J2, k02 / J2, k01 / J2, k11 / J2, k12 / J2, k02 / J2, k12 / J2, k22 / J2};
-  const double Wb = 0.25 * lam0 * (J2 - 1.0) - (0.5 * lam0 + mu0) * 0.5 * log(J2) + 0.5 * mu0 * (C[0] + C[4] + C[8] - 3.0);
+  double sa[6], ea;
+  aniso_base(ba, C, sa, ea);
+  const double Wb =
+      0.25 * lam0 * (J2 - 1.0) - (0.5 * lam0 + mu0) * 0.5 * log(J2) + 0.5 * mu0 * (C[0] + C[4] + C[8] - 3.0) + ea;
   ty[q] = (float)((Wbar[q] - Wb) / sg);
   for (int p = 0; p < 6; ++p) {
     const int I = kMandelI[p], J = kMandelJ[p];
     const double w = I == J ? 1.0 : 1.4142135623730950488;
-    const double sbase = 0.5 * lam0 * (J2 - 1.0) * Ci[3 * I + J] + mu0 * ((I == J ? 1.0 : 0.0) - Ci[3 * I + J]);
+    const double sbase = 0.5 * lam0 * (J2 - 1.0) * Ci[3 * I + J] + mu0 * ((I == J ? 1.0 : 0.0) - Ci[3 * I + J]) +
+                         sa[p] / w;
     const double ssym = 0.5 * (Sb[3 * I + J] + Sb[3 * J + I]);
     tg[(size_t)q * 6 + p] = (float)(sx / sg * w * (ssym - sbase));
     x[(size_t)q * 6 + p] = (float)(w * 0.5 * (C[3 * I + J] - (I == J ? 1.0 : 0.0)) / sx);
@@ -161,7 +204,7 @@ __global__ void targets_kernel(const double* F, const double* Pbar, const double
 }
 
 // list of the indices q with mask[q] == value (stable order), count in *count
-__global__ void compact_kernel(const int32_t* mask, int n, int value, int32_t* list, int32_t* count) {
+__global__ void compact_kernel(const int32_t* mask, int n, int value, int stride, int32_t* list, int32_t* count) {
   // one block: prefix count in chunks of blockDim
   __shared__ int32_t base;
   __shared__ int32_t warp_tot[32];
@@ -169,7 +212,7 @@ __global__ void compact_kernel(const int32_t* mask, int n, int value, int32_t* l
   __syncthreads();
   for (int start = 0; start < n; start += blockDim.x) {
     const int q = start + threadIdx.x;
-    const int flag = (q < n && mask[q] == value) ? 1 : 0;
+    const int flag = (q < n && mask[q] == value && (q % stride) == 0) ? 1 : 0;
     const unsigned ballot = __ballot_sync(0xffffffffu, flag);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int before = __popc(ballot & ((1u << lane) - 1u));
@@ -209,22 +252,32 @@ extern "C" int fehmm_surrogate_eval(fehmm_mlp* mlp, const fehmm_surrogate_params
   features_kernel<<<blocks, 128, 0, s>>>(F, n, sp->sx, sp->radius, x, inside);
   int rc = fehmm_mlp_eval(mlp, x, n, y, g, A ? H : nullptr, stream);
   if (rc != FEHMM_OK) return rc;
-  combine_kernel<<<blocks, 128, 0, s>>>(F, n, sp->lam0, sp->mu0, sp->sx, sp->sg, y, g, H, P, A, W);
+  BaseAniso ba;
+  for (int k = 0; k < 36; ++k) {
+    ba.Ca[k] = sp->Ca[k];
+    ba.H0[k] = sp->H0[k];
+  }
+  for (int k = 0; k < 6; ++k) ba.g0[k] = sp->g0[k];
+  ba.y0 = sp->y0;
+  combine_kernel<<<blocks, 128, 0, s>>>(F, n, sp->lam0, sp->mu0, sp->sx, sp->sg, ba, y, g, H, P, A, W);
   return cudaGetLastError() == cudaSuccess ? FEHMM_OK : FEHMM_ERR_CUDA;
 }
 
 extern "C" size_t fehmm_surrogate_work_floats(int n) { return (size_t)n * (6 + 1 + 6 + 36); }
 
-extern "C" int fehmm_select(const int32_t* mask, int n, int value, int32_t* list, int32_t* count, void* stream) {
-  if (!mask || !list || !count || n <= 0) return FEHMM_ERR_ARG;
-  compact_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(mask, n, value, list, count);
+extern "C" int fehmm_select(const int32_t* mask, int n, int value, int stride, int32_t* list, int32_t* count,
+                            void* stream) {
+  if (!mask || !list || !count || n <= 0 || stride < 1) return FEHMM_ERR_ARG;
+  compact_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(mask, n, value, stride, list, count);
   return cudaGetLastError() == cudaSuccess ? FEHMM_OK : FEHMM_ERR_CUDA;
 }
 
 extern "C" int fehmm_surrogate_targets(const fehmm_surrogate_params* sp, const double* F, const double* P,
                                        const double* W, int n, float* x, float* ty, float* tg, void* stream) {
   if (!sp || !F || !P || !W || !x || !ty || !tg || n <= 0 || !(sp->sx > 0) || !(sp->sg > 0)) return FEHMM_ERR_ARG;
-  targets_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(F, P, W, n, sp->lam0, sp->mu0, sp->sx, sp->sg, x, ty,
-                                                                    tg);
+  BaseAniso ba{};
+  for (int k = 0; k < 36; ++k) ba.Ca[k] = sp->Ca[k];
+  targets_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(F, P, W, n, sp->lam0, sp->mu0, sp->sx, sp->sg, ba, x,
+                                                                    ty, tg);
   return cudaGetLastError() == cudaSuccess ? FEHMM_OK : FEHMM_ERR_CUDA;
 }

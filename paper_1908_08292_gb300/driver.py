@@ -70,11 +70,15 @@ class LoadStepDriver:
         self._warm = set()
 
     # ------------------------------------------------------------ one iteration
+    def _constitutive(self, first):
+        """Pbar, Abar at every macro point: one batched RVE solve (overridden by the surrogate path)."""
+        self.ctx.rve_solve(self.F, self.P, self.A, self.st, self.it, flags=SOLVE_FROM_COMMITTED if first else 0)
+
     def _iteration(self, first, solve=True):
         c = self.ctx
         c.macro_update(self.u, self.du)
         c.macro_qp_F(self.u, self.F)
-        c.rve_solve(self.F, self.P, self.A, self.st, self.it, flags=SOLVE_FROM_COMMITTED if first else 0)
+        self._constitutive(first)
         c.macro_assemble(self.P, self.A, self.f, self.K)
         if solve:
             c.macro_solve(self.K, self.f, self.du, self.info, rtol=self.solve_rtol)

@@ -131,7 +131,30 @@ class MLP:
 
 class SurrogateParams(ctypes.Structure):
     _fields_ = [("lam0", ctypes.c_double), ("mu0", ctypes.c_double), ("sx", ctypes.c_double),
-                ("sg", ctypes.c_double), ("radius", ctypes.c_double)]
+                ("sg", ctypes.c_double), ("radius", ctypes.c_double), ("Ca", ctypes.c_double * 36),
+                ("y0", ctypes.c_double), ("g0", ctypes.c_double * 6), ("H0", ctypes.c_double * 36)]
+
+    def set_Ca(self, M):
+        M = np.asarray(M, dtype=np.float64).reshape(36)
+        for k in range(36):
+            self.Ca[k] = M[k]
+
+    def set_origin(self, mlp, hessian=False):
+        """Store the network's value and gradient (and optionally Hessian) at x = 0, evaluated by
+        the library, to be subtracted from the learned correction."""
+        import torch
+        dev = torch.device("cuda")
+        x = torch.zeros(1, 6, dtype=torch.float32, device=dev)
+        y = torch.zeros(1, dtype=torch.float32, device=dev)
+        g = torch.zeros(1, 6, dtype=torch.float32, device=dev)
+        H = torch.zeros(1, 6, 6, dtype=torch.float32, device=dev)
+        mlp.eval(x, y, g, H)
+        self.y0 = float(y.item())
+        gh, Hh = g.cpu().numpy().reshape(6), H.cpu().numpy().reshape(36)
+        for k in range(6):
+            self.g0[k] = float(gh[k])
+        for k in range(36):
+            self.H0[k] = float(0.5 * (Hh[k] + Hh[6 * (k % 6) + k // 6])) if hessian else 0.0
 
 
 def surrogate_eval(mlp: MLP, sp: SurrogateParams, F, P, A, W, inside, work, stream=None):
@@ -166,3 +189,185 @@ def surrogate_targets(sp: SurrogateParams, F, P, W, x, ty, tg, stream=None):
                                          _dev(P, torch.float64, "P", 9 * n), _dev(W, torch.float64, "W", n), n,
                                          _dev(x, torch.float32, "x", 6 * n), _dev(ty, torch.float32, "ty", n),
                                          _dev(tg, torch.float32, "tg", 6 * n), _stream(stream)), "surrogate_targets")
+
+
+# ----------------------------------------------------------------------------- pipeline
+def fixed_rve_context(n_qp, precision="mixed", grid=12, **options):
+    """A 3D context whose n_qp points all use the fixed two-inclusion microstructure (grid^3)."""
+    import synth
+    phase, _ = synth.fixed_rve12(n=grid)
+    ctx = Context(3, precision, **options)
+    ctx.add_rves([grid], [phase], [[1.0, 10.0]], [[0.3, 0.3]])
+    ctx.bind_qps(np.zeros(n_qp, dtype=np.int32))
+    return ctx
+
+
+def rve_solve_batch(ctx, F, with_tangent=False, with_energy=True, stages=1):
+    """Full RVE solves at the deformation gradients F (device [n][9], n = ctx.n_qp) from zero
+    fluctuations, reached in `stages` equal increments of F - I (load continuation; each
+    stage warm-starts from the previous one).  Returns device tensors P, A (or None), W, status."""
+    import torch
+
+    from . import SOLVE_ENERGY, SOLVE_FROM_COMMITTED, SOLVE_NO_TANGENT
+    n = ctx.n_qp
+    dev = F.device
+    P = torch.zeros(n, 9, dtype=torch.float64, device=dev)
+    A = torch.zeros(n, 81, dtype=torch.float64, device=dev) if with_tangent else None
+    W = torch.zeros(n, dtype=torch.float64, device=dev)
+    st = torch.zeros(n, dtype=torch.int32, device=dev)
+    it = torch.zeros(n, 4, dtype=torch.int32, device=dev)
+    eye = torch.eye(3, dtype=torch.float64, device=dev).reshape(1, 9)
+    for k in range(1, stages + 1):
+        last = k == stages
+        Fk = F if last else (eye + (k / stages) * (F - eye)).contiguous()
+        flags = (SOLVE_FROM_COMMITTED if k == 1 else 0) | (SOLVE_ENERGY if (with_energy and last) else 0)
+        flags |= 0 if (with_tangent and last) else SOLVE_NO_TANGENT
+        ctx.rve_solve(Fk, P, A if last else None, st, it, W=W if last else None, flags=flags)
+    return P, A, W, st
+
+
+def mandel4(A):
+    """6x6 Mandel matrix of a fourth-order tensor with minor symmetries (order 11,22,33,23,13,12)."""
+    A = np.asarray(A).reshape(3, 3, 3, 3)
+    w = [1.0 if i == j else SQ2 for i, j in MANDEL]
+    return np.array([[A[i, j, k, l] * w[p] * w[q] for q, (k, l) in enumerate(MANDEL)] for p, (i, j) in enumerate(MANDEL)])
+
+
+def base_law(ctx_one):
+    """Base energy of the surrogate from the small-strain homogenised tangent A0 (F = I):
+    (lam0, mu0) its isotropic projection, Ca = Mandel(A0 - CC_iso(lam0, mu0)) the remainder.
+    Host arithmetic on the 81 entries of A0 (set-up)."""
+    import torch
+    F = torch.eye(3, dtype=torch.float64, device="cuda").reshape(1, 9).repeat(ctx_one.n_qp, 1).contiguous()
+    P, A, W, st = rve_solve_batch(ctx_one, F, with_tangent=True, with_energy=False)
+    A0 = A[0].cpu().numpy().reshape(3, 3, 3, 3)
+    A0 = 0.25 * (A0 + A0.transpose(1, 0, 2, 3) + A0.transpose(0, 1, 3, 2) + A0.transpose(1, 0, 3, 2))
+    lam0, mu0 = isotropic_projection(A0)
+    I = np.eye(3)
+    iso = lam0 * np.einsum("ij,kl->ijkl", I, I) + mu0 * (np.einsum("ik,jl->ijkl", I, I) + np.einsum("il,jk->ijkl", I, I))
+    return lam0, mu0, mandel4(A0 - iso)
+
+
+def generate(ctx, sp, U, chunk=None, stages=3, drop_failed=True):
+    """Training data from full GPU RVE solves at F = U (host array (N, 3, 3)): device float32
+    features x (N, 6), targets ty (N,), tg (N, 6), plus the FP64 P, W of the solves and the
+    number of samples dropped because their RVE solve failed (status > 1, reported)."""
+    import torch
+    N = U.shape[0]
+    chunk = ctx.n_qp if chunk is None else chunk
+    dev = torch.device("cuda")
+    x = torch.zeros(N, 6, dtype=torch.float32, device=dev)
+    ty = torch.zeros(N, dtype=torch.float32, device=dev)
+    tg = torch.zeros(N, 6, dtype=torch.float32, device=dev)
+    Ps = torch.zeros(N, 9, dtype=torch.float64, device=dev)
+    Ws = torch.zeros(N, dtype=torch.float64, device=dev)
+    bad = 0
+    hist = np.zeros(8, dtype=np.int64)
+    ok = torch.ones(N, dtype=torch.bool, device=dev)
+    for s0 in range(0, N, chunk):
+        m = min(chunk, N - s0)
+        Fh = np.zeros((ctx.n_qp, 9))
+        Fh[:, [0, 4, 8]] = 1.0
+        Fh[:m] = U[s0:s0 + m].reshape(m, 9)
+        F = torch.tensor(Fh, device=dev)
+        P, _, W, st = rve_solve_batch(ctx, F, stages=stages)
+        ok[s0:s0 + m] = st[:m] <= 1
+        sts = st[:m].cpu().numpy()
+        bad += int((sts > 1).sum())
+        hist += np.bincount(np.clip(sts, 0, 7), minlength=8)
+        surrogate_targets(sp, F[:m].contiguous(), P[:m].contiguous(), W[:m].contiguous(), x[s0:s0 + m],
+                          ty[s0:s0 + m], tg[s0:s0 + m])
+        Ps[s0:s0 + m] = P[:m]
+        Ws[s0:s0 + m] = W[:m]
+    if bad and not drop_failed:
+        raise FehmmError(f"{bad} training RVE solves failed (status counts {hist.tolist()})")
+    if bad:
+        x, ty, tg, Ps, Ws = (t[ok].contiguous() for t in (x, ty, tg, Ps, Ws))
+    return x, ty, tg, Ps, Ws, bad
+
+
+def train(mlp, x, ty, tg, epochs, batch=4096, lr=2e-3, lr_end=2e-5, weight_decay=0.0, cg_weight=1.0, log=None):
+    """AdamW over contiguous batches of i.i.d. samples; cosine learning-rate decay.  Loss weights
+    normalise each term by its target's mean square."""
+    import torch
+    N = x.shape[0]
+    cy = 1.0 / max(float((ty.double() ** 2).mean().item()), 1e-30) / batch
+    cgw = cg_weight / max(float((tg.double() ** 2).sum(1).mean().item()), 1e-30) / batch
+    steps = epochs * max(1, N // batch)
+    loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+    hist = []
+    k = 0
+    for ep in range(epochs):
+        for s0 in range(0, N - batch + 1, batch):
+            t = k / max(1, steps - 1)
+            rate = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * t))
+            mlp.loss_grad(x[s0:s0 + batch], ty[s0:s0 + batch], tg[s0:s0 + batch], cy, cgw, loss)
+            mlp.adamw(rate, weight_decay=weight_decay)
+            k += 1
+        hist.append(float(loss.item()))
+        if log:
+            log(f"epoch {ep} loss {hist[-1]:.3e}")
+    return hist
+
+
+def stress_errors(P_s, P_ref, floor):
+    """Relative Frobenius stress errors |P_s - P_ref| / max(|P_ref|, floor) per point (host)."""
+    P_s = np.asarray(P_s).reshape(-1, 9)
+    P_ref = np.asarray(P_ref).reshape(-1, 9)
+    return np.linalg.norm(P_s - P_ref, axis=1) / np.maximum(np.linalg.norm(P_ref, axis=1), floor)
+
+
+class SurrogateDriver:
+    """Load steps of a macro problem whose constitutive step is the surrogate with fallback:
+    the surrogate gives Pbar, Abar at every point; points outside the trust region are replaced
+    by full RVE solves (fehmm_select + fehmm_rve_solve_list), and every `audit_stride`-th point
+    inside is also solved fully into separate arrays so that the surrogate's error is measured
+    online.  All steps are library kernels."""
+
+    def __init__(self, problem, mlp, sp, audit_stride=0, **options):
+        import torch
+
+        from . import select
+        from .driver import LoadStepDriver
+        self._select = select
+        drv = LoadStepDriver(problem, **options)
+        self.drv = drv
+        self.mlp, self.sp = mlp, sp
+        n = problem.n_qp
+        dev = drv.u.device
+        self.inside = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.work = torch.zeros(work_floats(n), dtype=torch.float32, device=dev)
+        self.lst = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.audit_stride = audit_stride
+        if audit_stride:
+            self.alst = torch.zeros(n, dtype=torch.int32, device=dev)
+            self.acnt = torch.zeros(1, dtype=torch.int32, device=dev)
+            self.Pa = torch.zeros_like(drv.P)
+            self.Aa = torch.zeros_like(drv.A)
+            self.sta = torch.zeros_like(drv.st)
+            self.ita = torch.zeros_like(drv.it)
+        drv._constitutive = self._constitutive
+        self.fallback = []
+        self.audit = []
+
+    def _constitutive(self, first):
+        from . import SOLVE_FROM_COMMITTED
+        d = self.drv
+        flags = SOLVE_FROM_COMMITTED if first else 0
+        surrogate_eval(self.mlp, self.sp, d.F, d.P, d.A, None, self.inside, self.work)
+        d.st.zero_()
+        self._select(self.inside, 0, self.lst, self.cnt)
+        d.ctx.rve_solve_list(d.F, d.P, d.A, d.st, d.it, flags, self.lst, self.cnt)
+        if self.audit_stride:
+            self._select(self.inside, 1, self.alst, self.acnt, stride=self.audit_stride)
+            d.ctx.rve_solve_list(d.F, self.Pa, self.Aa, self.sta, self.ita, flags, self.alst, self.acnt)
+
+    def audit_errors(self, floor):
+        """Stress errors of the surrogate at the audited points of the last constitutive step."""
+        k = int(self.acnt.item())
+        idx = self.alst[:k].long()
+        return stress_errors(self.drv.P[idx].cpu().numpy(), self.Pa[idx].cpu().numpy(), floor)
+
+    def fallback_count(self):
+        return int(self.cnt.item())

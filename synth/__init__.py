@@ -195,11 +195,12 @@ def config3(macro: int = 8, seed: int = 1003, sizes=(8, 12, 16), n_rve: int | No
                    extra={"n_incl": n_incl, "phi_target": phi})
 
 
-def fixed_rve12(seed: int = 1004) -> tuple:
-    """The fixed 12^3 two-inclusion microstructure (config-3 generator, n_incl = 2)."""
+def fixed_rve12(seed: int = 1004, n: int = 12) -> tuple:
+    """The fixed two-inclusion microstructure (config-3 generator, n_incl = 2) on an n^3 grid
+    (12^3 in the workloads; smaller grids of the same geometry serve quick tests)."""
     u = uniform(seed, np.array([0]), 7)[0]
     phi = 0.1 + 0.2 * u[0]
-    return sphere_rve(12, 2, phi, u[1:7].reshape(2, 3)), phi
+    return sphere_rve(n, 2, phi, u[1:7].reshape(2, 3)), phi
 
 
 def config5(macro: int = 16) -> Problem:

@@ -89,6 +89,13 @@ def test_surrogate_eval_and_trust_region():
     m = MLP(n)
     m.set_params(p)
     sp = SurrogateParams(lam0, mu0, sx, sg, radius)
+    M = synth.random_field(63, 6, 6, 0.1)
+    Ca = M + M.T
+    sp.set_Ca(Ca)
+    y0, g0 = 0.02, synth.random_field(64, 1, 6, 0.05)[0]
+    sp.y0 = y0
+    for k in range(6):
+        sp.g0[k] = g0[k]
     Ft = torch.tensor(F.reshape(n, 9), device=dev)
     P = torch.zeros(n, 9, dtype=torch.float64, device=dev)
     A = torch.zeros(n, 81, dtype=torch.float64, device=dev)
@@ -97,7 +104,7 @@ def test_surrogate_eval_and_trust_region():
     work = torch.zeros(work_floats(n), dtype=torch.float32, device=dev)
     surrogate_eval(m, sp, Ft, P, A, W, inside, work)
     torch.cuda.synchronize()
-    Wr, Pr, Ar = osur.evaluate(p, F, lam0, mu0, sx, sg, bf16=True)
+    Wr, Pr, Ar = osur.evaluate(p, F, lam0, mu0, sx, sg, bf16=True, Ca=Ca, origin=(y0, g0, np.zeros((6, 6))))
     d = osur.stretch_distance(F)
     ins = inside.cpu().numpy()
     clear = np.abs(d - radius) > 1e-9
@@ -105,12 +112,15 @@ def test_surrogate_eval_and_trust_region():
     assert 0 < ins.sum() < n  # both sides of the trust boundary are exercised
     # the base law is evaluated in FP64 on both sides; the network part (sg y and its derivatives)
     # carries the bfloat16 budget: a few 2^-8 units relative to its own size
-    from oracle import material as mat
-    Wb, Pb, Ab = mat.psi(F, lam0, mu0), mat.P_of_F(F, lam0, mu0), mat.A_of_F(F, lam0, mu0)
+    zero_net = {k: np.zeros_like(v) for k, v in p.items()}
+    Wb, Pb, Ab = osur.evaluate(zero_net, F, lam0, mu0, sx, sg, Ca=Ca)  # base law only
     assert np.linalg.norm(W.cpu().numpy() - Wr) < 8e-3 * np.linalg.norm(Wr - Wb)
     assert np.linalg.norm(P.cpu().numpy() - Pr.reshape(n, 9)) < 8e-3 * np.linalg.norm((Pr - Pb).reshape(n, 9))
     assert np.linalg.norm(A.cpu().numpy() - Ar.reshape(n, 81)) < 1.6e-2 * np.linalg.norm((Ar - Ab).reshape(n, 81))
-    # with a zero network the surrogate is exactly the base law
+    # with a zero network (and no origin shift) the surrogate is exactly the base law
+    sp.y0 = 0.0
+    for k in range(6):
+        sp.g0[k] = 0.0
     m.set_params(np.zeros_like(m.get_params()))
     surrogate_eval(m, sp, Ft, P, A, W, inside, work)
     torch.cuda.synchronize()

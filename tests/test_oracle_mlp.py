@@ -71,14 +71,18 @@ def test_surrogate_chain_rule_fd():
             p[k] = 0.05 * synth.random_field(22, 1, p[k].size, 1.0)[0]
     F = synth.random_F(23, 2, 3, 0.12)
     lam0, mu0, sx, sg = 1.2, 0.8, 0.35, 0.05
-    W, P, A = sur.evaluate(p, F, lam0, mu0, sx, sg)
+    M = synth.random_field(24, 6, 6, 0.1)
+    Ca = M + M.T
+    origin = (0.01, synth.random_field(25, 1, 6, 0.02)[0], np.zeros((6, 6)))
+    kw = dict(Ca=Ca, origin=origin)
+    W, P, A = sur.evaluate(p, F, lam0, mu0, sx, sg, **kw)
     h = 1e-6
     for k in range(3):
         for l in range(3):
             E = np.zeros((3, 3))
             E[k, l] = h
-            Wp, Pp, _ = sur.evaluate(p, F + E, lam0, mu0, sx, sg)
-            Wm, Pm, _ = sur.evaluate(p, F - E, lam0, mu0, sx, sg)
+            Wp, Pp, _ = sur.evaluate(p, F + E, lam0, mu0, sx, sg, **kw)
+            Wm, Pm, _ = sur.evaluate(p, F - E, lam0, mu0, sx, sg, **kw)
             np.testing.assert_allclose((Wp - Wm) / (2 * h), P[:, k, l], atol=2e-8)
             np.testing.assert_allclose((Pp - Pm) / (2 * h), A[:, :, :, k, l], atol=2e-7)
 
