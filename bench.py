@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RVE solves/s (micro-DOF*Newton-iter/s reported alongside)"
-_SIZE = {"macro": 32, "workload": "c2"}
+_SIZE = {"macro": 32, "workload": "c2", "world": 1}
 UNIT = "RVE solves/s"
 MACRO, RVE_N, N_STEPS = 32, 32, 20
 MACRO_C3, N_STEPS_C3 = 8, 10
@@ -58,12 +58,17 @@ def workload_config(step_index):
                             f"launch, macro iteration 1 of load step {step_index}/{N_STEPS_C3} (uniaxial to 20%)",
                 "n_qp": MACRO ** 3 * 8, "rve_grid": "8/12/16 mixed", "load_step": step_index,
                 "l2": "flushed (256 MB write) between timed steps"}
-    return {"workload": f"2D plane-strain FE-HMM macro {MACRO}x{MACRO} Q1 ({MACRO * MACRO * 4} qps), "
-                        f"one {RVE_N}x{RVE_N} Q1 periodic RVE per qp (random circular inclusion r~U(0.15,0.35), "
-                        f"E ratio log-U[5,50]), neo-Hookean, mixed FP32/FP64, macro iteration 1 of load step "
-                        f"{step_index}/{N_STEPS} (biaxial 30% + shear 0.3)",
-            "n_qp": MACRO * MACRO * 4, "rve_grid": RVE_N, "micro_dofs_per_rve": 2 * RVE_N * RVE_N,
-            "load_step": step_index, "l2": "flushed (256 MB write) between timed steps"}
+    W = _SIZE["world"]
+    cfg = {"workload": f"2D plane-strain FE-HMM macro {MACRO}x{MACRO * W} Q1 ({MACRO * MACRO * W * 4} qps), "
+                       f"one {RVE_N}x{RVE_N} Q1 periodic RVE per qp (random circular inclusion r~U(0.15,0.35), "
+                       f"E ratio log-U[5,50]), neo-Hookean, mixed FP32/FP64, macro iteration 1 of load step "
+                       f"{step_index}/{N_STEPS} (biaxial 30% + shear 0.3)",
+           "n_qp": MACRO * MACRO * W * 4, "rve_grid": RVE_N, "micro_dofs_per_rve": 2 * RVE_N * RVE_N,
+           "load_step": step_index, "l2": "flushed (256 MB write) between timed steps"}
+    if W > 1:
+        cfg["parallelism"] = (f"dp{W}: macro elements in {W} contiguous blocks balanced by RVE dofs, one per rank; "
+                              "all-reduce of f and K, macro solve on rank 0, broadcast of du")
+    return cfg
 
 
 def dist_env():
@@ -128,18 +133,25 @@ def build_problem(step_index):
         p = synth.config3(macro=_SIZE["macro"])
         F = np.diag([1.0 + 0.2 * step_index / N_STEPS_C3, 1.0, 1.0])
         return p, F
-    p = synth.config2(macro=_SIZE["macro"], rve=RVE_N)
+    p = synth.config2(macro=_SIZE["macro"], rve=RVE_N, macro_y=_SIZE["macro"] * _SIZE["world"])
     lam = step_index / N_STEPS
     F = np.eye(2) + lam * (p.extra["F_end"] - np.eye(2))
     return p, F
 
 
+def macro_n(d):
+    """Macro elements per axis: a square/cubic mesh, taller in y by the rank count (2D weak scaling)."""
+    n = [_SIZE["macro"]] * d
+    if d == 2:
+        n[1] *= _SIZE["world"]
+    return n
+
+
 def macro_affine_u(F):
     """u = (F - I) X at the macro nodes (x fastest)."""
-    MACRO = _SIZE["macro"]
     d = F.shape[0]
-    ax = np.arange(MACRO + 1) / MACRO
-    X = np.stack(np.meshgrid(*([ax] * d), indexing="ij"), -1)
+    axes = [np.arange(m + 1) / m for m in macro_n(d)]
+    X = np.stack(np.meshgrid(*axes, indexing="ij"), -1)
     X = X.transpose(*range(d - 1, -1, -1), d).reshape(-1, d)
     return (X @ (F - np.eye(d)).T).reshape(-1)
 
@@ -177,6 +189,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    _SIZE["world"] = world if _SIZE["workload"] == "c2" else 1
     fe.lib()
     p, Fload = build_problem(args.step_index)
     n_qp = p.n_qp
@@ -185,28 +198,60 @@ def run_gpu(args):
     ctx = fe.Context(d, "mixed", **opts)
     ctx.add_rves(p.rve_n, p.rve_phase, p.rve_E, p.rve_nu)
     ctx.bind_qps(p.qp_rve)
-    ctx.macro_create([_SIZE["macro"]] * d)
+    ctx.macro_create(macro_n(d))
     ctx.macro_set_dirichlet(p.dirichlet_dofs, p.dirichlet_end)
     _, _, n_rows, nnz = ctx.macro_csr()
     u_h = torch.tensor(macro_affine_u(Fload), dtype=torch.float64).pin_memory()
     u = u_h.to(dev)
-    F = torch.empty(n_qp, d * d, dtype=torch.float64, device=dev)
-    P = torch.empty(n_qp, d * d, dtype=torch.float64, device=dev)
-    A = torch.empty(n_qp, d ** 4, dtype=torch.float64, device=dev)
-    st = torch.empty(n_qp, dtype=torch.int32, device=dev)
-    it = torch.empty(n_qp, 4, dtype=torch.int32, device=dev)
-    f = torch.empty(n_rows, dtype=torch.float64, device=dev)
-    K = torch.empty(nnz, dtype=torch.float64, device=dev)
-    du = torch.empty(n_rows, dtype=torch.float64, device=dev)
-    info = torch.empty(3, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    if _SIZE["world"] > 1:
+        # weak scaling: the macro mesh is `world` times taller, each rank solves the RVEs of its
+        # contiguous block of macro elements; one sum of f and K per iteration, rank 0 solves
+        from paper_1908_08292_gb300.dist import Shard, ShardedIteration
+        dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve])
+        shard = Shard.make(rank, world, dofs, 2 ** d)
+        sit = ShardedIteration(ctx, shard, n_qp, d, dev)
+        F, P, A, st, it, f, K, du, info = sit.F, sit.P, sit.A, sit.st, sit.it, sit.f, sit.K, sit.du, sit.info
+        mine = shard.qps.astype(np.int64)
+
+        def rve_phase():
+            ctx.rve_solve_list(F, P, A, st, it, fe.SOLVE_FROM_COMMITTED, sit.lst, sit.cnt)
+
+        def assemble_phase():
+            ctx.macro_assemble(P, A, f, K)
+            shard.reduce_system(f, K)
+
+        def solve_phase():
+            if rank == 0:
+                ctx.macro_solve(K, f, du, info, rtol=1e-10)
+            shard.share_correction(du)
+    else:
+        F = torch.empty(n_qp, d * d, dtype=torch.float64, device=dev)
+        P = torch.empty(n_qp, d * d, dtype=torch.float64, device=dev)
+        A = torch.empty(n_qp, d ** 4, dtype=torch.float64, device=dev)
+        st = torch.empty(n_qp, dtype=torch.int32, device=dev)
+        it = torch.empty(n_qp, 4, dtype=torch.int32, device=dev)
+        f = torch.empty(n_rows, dtype=torch.float64, device=dev)
+        K = torch.empty(nnz, dtype=torch.float64, device=dev)
+        du = torch.empty(n_rows, dtype=torch.float64, device=dev)
+        info = torch.empty(3, dtype=torch.float64, device=dev)
+        mine = np.arange(n_qp)
+
+        def rve_phase():
+            ctx.rve_solve(F, P, A, st, it, flags=fe.SOLVE_FROM_COMMITTED)
+
+        def assemble_phase():
+            ctx.macro_assemble(P, A, f, K)
+
+        def solve_phase():
+            ctx.macro_solve(K, f, du, info, rtol=1e-10)
 
     def step():
         ctx.macro_qp_F(u, F)
-        ctx.rve_solve(F, P, A, st, it, flags=fe.SOLVE_FROM_COMMITTED)
-        ctx.macro_assemble(P, A, f, K)
-        ctx.macro_solve(K, f, du, info, rtol=1e-10)
+        rve_phase()
+        assemble_phase()
+        solve_phase()
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -224,11 +269,11 @@ def run_gpu(args):
             e0.record(stream)
             ctx.macro_qp_F(u, F)
             e1.record(stream)
-            ctx.rve_solve(F, P, A, st, it, flags=fe.SOLVE_FROM_COMMITTED)
+            rve_phase()
             e2.record(stream)
-            ctx.macro_assemble(P, A, f, K)
+            assemble_phase()
             e3.record(stream)
-            ctx.macro_solve(K, f, du, info, rtol=1e-10)
+            solve_phase()
             e4.record(stream)
         torch.cuda.synchronize()
     launches = ctx.launches - launches0
@@ -240,8 +285,8 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
         dist.barrier()
-    status = st.cpu().numpy()
-    iters = it.cpu().numpy()
+    status = st.cpu().numpy()[mine]
+    iters = it.cpu().numpy()[mine]
     ok = int((status == 0).sum())
     # ---- end-to-end through the public API with host buffers (H2D of u, D2H of results)
     f_h = torch.empty(n_rows, dtype=torch.float64).pin_memory()
@@ -269,9 +314,9 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    n_total = n_qp * world
+    n_total = n_qp if _SIZE["world"] > 1 else n_qp * world  # sharded mesh, or one replica per rank
     value = n_total / (t_step / args.steps)
-    dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve], dtype=np.float64)
+    dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve[mine]], dtype=np.float64)
     dof_iter = float((dofs * iters[:, 0].astype(np.float64)).sum()) * world / (t_step / args.steps)
     f64, f32 = flops_2d(RVE_N, iters) if d == 2 else flops_3d(p, iters)
     t_rve = statistics.mean(rve_ms) / 1e3
@@ -355,6 +400,200 @@ def run_reference(args):
     }))
 
 
+def _u_ball_problem(macro):
+    """Config-5 macro problem (macro^3 Hex8, fixed 12^3 RVE at every point)."""
+    import synth
+    return synth.config5(macro=macro)
+
+
+def run_c4(args):
+    """Surrogate training workload: GPU RVE solves at U uniform in |U - I| <= 0.3 on the fixed 12^3
+    two-inclusion RVE (training targets), training with the library's BF16 kernels, held-out
+    stress error (GPU-solved held-out set; a few points re-verified by the FP64 CPU oracle)."""
+    import torch
+
+    import synth
+    from paper_1908_08292_gb300 import surrogate as su
+    torch.cuda.set_device(0)
+    one = su.fixed_rve_context(1)
+    lam0, mu0, Ca = su.base_law(one)
+    sp = su.SurrogateParams(lam0, mu0, 0.35, 0.01 * (lam0 + 2 * mu0), 0.3)
+    sp.set_Ca(Ca)
+    ctx = su.fixed_rve_context(4096)
+    U = synth.stretch_ball(1004, args.c4_samples, 0.3)
+    Uh = synth.stretch_ball(2004, args.c4_holdout, 0.3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, ty, tg, P, W, dropped = su.generate(ctx, sp, U)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    _, _, _, Ph, Wh, dropped_h = su.generate(ctx, sp, Uh)
+    mlp = su.MLP(4096)
+    mlp.set_params(su.init_params(7))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    steps = args.c4_epochs * (x.shape[0] // 4096)
+    sp.set_origin(mlp)
+    n = Uh.shape[0]
+    Fh = torch.tensor(Uh.reshape(n, 9), device="cuda")
+    Ps = torch.zeros(n, 9, dtype=torch.float64, device="cuda")
+    As = torch.zeros(n, 81, dtype=torch.float64, device="cuda")
+    ins = torch.zeros(n, dtype=torch.int32, device="cuda")
+    m2 = su.MLP(n)
+    m2.set_params(mlp.get_params())
+    work = torch.zeros(su.work_floats(n), dtype=torch.float32, device="cuda")
+    su.surrogate_eval(m2, sp, Fh, Ps, As, None, ins, work)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    su.surrogate_eval(m2, sp, Fh, Ps, As, None, ins, work)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t2
+    e = su.stress_errors(Ps.cpu().numpy(), Ph.cpu().numpy(), 1e-3)
+    verified = []
+    if args.c4_verify > 0:  # FP64 CPU oracle on a few held-out points (test infrastructure)
+        from oracle.rve import PeriodicRVE
+        ph, _ = synth.fixed_rve12()
+        rve = PeriodicRVE(12, 3, ph, [1.0, 10.0], [0.3, 0.3])
+        for q in range(args.c4_verify):
+            w = None  # same three-stage load continuation as the GPU data generation
+            for t in (1.0 / 3.0, 2.0 / 3.0, 1.0):
+                r = rve.solve(np.eye(3) + t * (Uh[q] - np.eye(3)), w, rtol=1e-10, tangent=False)
+                w = r["w"]
+            if "P" in r:
+                verified.append(float(np.linalg.norm(Ph[q].cpu().numpy().reshape(3, 3) - r["P"]) /
+                                      np.linalg.norm(r["P"])))
+    print(json.dumps({
+        "metric": "surrogate training: RVE solves/s for training data; held-out relative stress error",
+        "value": x.shape[0] / t_data, "unit": "RVE solves/s (12^3, 3-stage continuation)", "n_gpus": 1,
+        "higher_is_better": True, "workload": "c4",
+        "config": {"workload": f"fixed 12^3 two-inclusion RVE (ratio 10), {args.c4_samples} training U in "
+                               f"|U-I|_F<=0.3, {args.c4_holdout} held-out, MLP 6-4x128 SiLU-1 BF16/FP32, AdamW "
+                               f"batch 4096, {args.c4_epochs} epochs, Sobolev loss (W and S)"},
+        "dropped_failed_solves": dropped + dropped_h, "base_law": {"lam0": lam0, "mu0": mu0},
+        "train_seconds": t_train, "train_steps_per_s": steps / t_train, "loss_first_last": [hist[0], hist[-1]],
+        "heldout_stress_err": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max()),
+                               "median": float(np.median(e)), "n": int(n)},
+        "inference_points_per_s": n / t_inf, "oracle_verified_gpu_heldout_rel_err": verified,
+        "target_1e-4_met": bool(e.max() <= 1e-4),
+    }))
+
+
+def run_c5(args):
+    """Config 5: one macro iteration of the surrogate-with-fallback path vs the plain GPU RVE path
+    from the same macro state (macro^3 Hex8, the fixed 12^3 RVE everywhere)."""
+    import torch
+
+    import synth
+    from paper_1908_08292_gb300 import SOLVE_FROM_COMMITTED
+    from paper_1908_08292_gb300 import surrogate as su
+    torch.cuda.set_device(0)
+    one = su.fixed_rve_context(1)
+    lam0, mu0, Ca = su.base_law(one)
+    sp = su.SurrogateParams(lam0, mu0, 0.35, 0.01 * (lam0 + 2 * mu0), args.c5_radius)
+    sp.set_Ca(Ca)
+    gen = su.fixed_rve_context(4096)
+    x, ty, tg, _, _, _ = su.generate(gen, sp, synth.stretch_ball(1004, args.c4_samples, 0.3))
+    mlp = su.MLP(max(4096, args.macro ** 3 * 8))
+    mlp.set_params(su.init_params(7))
+    su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096)
+    sp.set_origin(mlp)
+    gen.close()
+    p = _u_ball_problem(args.macro)
+    drv = su.SurrogateDriver(p, mlp, sp, audit_stride=args.c5_audit_stride, precision="mixed", newton_rtol=1e-8)
+    d = drv.drv
+    for k in range(1, args.c5_step):  # reach the state of load step c5_step with the surrogate path
+        d.load_step(k)
+    d.scale = args.c5_step / p.n_steps
+    d.ctx.macro_apply_dirichlet(d.u, d.du, d.scale)
+    n = p.n_qp
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def surrogate_iteration():
+        d.ctx.macro_qp_F(d.u, d.F)
+        drv._constitutive(True)
+        d.ctx.macro_assemble(d.P, d.A, d.f, d.K)
+        d.ctx.macro_solve(d.K, d.f, d.du, d.info, rtol=1e-10)
+
+    def plain_iteration():
+        d.ctx.macro_qp_F(d.u, d.F)
+        d.ctx.rve_solve(d.F, d.P, d.A, d.st, d.it, flags=SOLVE_FROM_COMMITTED)
+        d.ctx.macro_assemble(d.P, d.A, d.f, d.K)
+        d.ctx.macro_solve(d.K, d.f, d.du, d.info, rtol=1e-10)
+
+    surrogate_iteration()  # warm-up
+    t_s = min(timed(surrogate_iteration) for _ in range(max(1, args.steps)))
+    fallback = drv.fallback_count()
+    audit = drv.audit_errors(1e-3) if args.c5_audit_stride else np.zeros(0)
+    P_sur = d.P.clone()
+    t_p = timed(plain_iteration)
+    st = d.st.cpu().numpy()
+    e = su.stress_errors(P_sur.cpu().numpy(), d.P.cpu().numpy(), 1e-3)
+    print(json.dumps({
+        "metric": "macro Newton iterations/s, surrogate+fallback vs plain GPU RVE path",
+        "value": 1.0 / t_s, "unit": "macro iterations/s", "n_gpus": 1, "higher_is_better": True,
+        "workload": "c5",
+        "config": {"workload": f"macro {args.macro}^3 Hex8 ({n} qps), fixed 12^3 two-inclusion RVE at every qp, "
+                               f"clamped at x=0, shear+tension to |F-I|=0.35 in {p.n_steps} steps; state of load "
+                               f"step {args.c5_step}; trust radius {args.c5_radius}"},
+        "plain_value": 1.0 / t_p, "gain": t_p / t_s, "seconds": {"surrogate": t_s, "plain": t_p},
+        "fallback_points": fallback, "fallback_fraction": fallback / n, "plain_status_ok": int((st == 0).sum()),
+        "audit": {"n": int(audit.size), "rms": float(np.sqrt((audit ** 2).mean())) if audit.size else None,
+                  "max": float(audit.max()) if audit.size else None},
+        "stress_err_vs_plain": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())},
+        "target_1e-4_met": bool(e.max() <= 1e-4),
+    }))
+
+
+def run_schemes(args):
+    """Algorithm 1 (nested) vs Algorithm 2 (alternating) on full load paths: macro iterations,
+    micro Newton iterations and wall time per scheme (the structure of the paper's speed-up
+    tables; synthetic microstructures stand in for the paper's)."""
+    import torch
+
+    import synth
+    from paper_1908_08292_gb300.driver import LoadStepDriver
+    torch.cuda.set_device(0)
+    cases = [("c1 2D 4x4 Q1 macro, 64 qps, 8x8 RVE (FP64), 10 steps", synth.config1(), 10, {}),
+             ("c2-shaped 2D 8x8 Q1 macro, 256 qps, 32x32 RVEs (mixed), 5 of 20 steps",
+              synth.config2(macro=8, rve=32), 5, {}),
+             ("c3-shaped 3D 4^3 Hex8 macro, 512 qps, 8/12/16^3 RVEs (mixed), 4 of 10 steps",
+              synth.config3(macro=4), 4, {})]
+    out = []
+    for name, p, steps, opts in cases:
+        row = {"case": name}
+        for scheme in ("nested", "alternating"):
+            drv = LoadStepDriver(p, scheme=scheme, graphs=True, **opts)
+            drv.load_step(1)  # warm-up: module load, graph capture (state then restarts)
+            drv.close()
+            drv = LoadStepDriver(p, scheme=scheme, graphs=True, **opts)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            recs = drv.run(steps)
+            torch.cuda.synchronize()
+            row[scheme] = {"seconds": time.perf_counter() - t0,
+                           "macro_iters": int(sum(r["macro_iters"] for r in recs)),
+                           "micro_newton_iters": int(sum(sum(r["micro_newton"]) for r in recs)),
+                           "all_converged": bool(all(r["converged"] for r in recs)),
+                           "macro_iters_per_step": [r["macro_iters"] for r in recs]}
+            drv.close()
+        row["speedup_alternating"] = row["nested"]["seconds"] / row["alternating"]["seconds"]
+        out.append(row)
+    print(json.dumps({"metric": "load-path wall time, nested (Algorithm 1) vs alternating (Algorithm 2)",
+                      "workload": "schemes", "n_gpus": 1, "unit": "s", "higher_is_better": False, "cases": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,13 +607,30 @@ def main():
     ap.add_argument("--cg-rtol", type=float, default=None, help="override the Newton-correction PCG tolerance")
     ap.add_argument("--cond-rtol", type=float, default=None, help="override the tangent-transfer PCG tolerance")
     ap.add_argument("--macro", type=int, default=None, help="macro elements per axis (profiling runs use less)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: 2D 4096 RVEs of 32x32 (default, the headline); c3: 3D 4096 uneven Hex8 RVEs")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "schemes"],
+                    help="c2: 2D 4096 RVEs of 32x32 (default, the headline); c3: 3D 4096 uneven Hex8 RVEs; "
+                         "c4: surrogate training; c5: surrogate+fallback vs plain macro iteration; "
+                         "schemes: nested vs alternating load paths")
+    ap.add_argument("--c4-samples", type=int, default=40960)
+    ap.add_argument("--c4-holdout", type=int, default=10240)
+    ap.add_argument("--c4-epochs", type=int, default=600)
+    ap.add_argument("--c4-verify", type=int, default=0, help="held-out points re-solved by the CPU oracle")
+    ap.add_argument("--c5-radius", type=float, default=0.3)
+    ap.add_argument("--c5-step", type=int, default=10)
+    ap.add_argument("--c5-audit-stride", type=int, default=64)
     args = ap.parse_args()
     _SIZE["workload"] = args.workload
     _SIZE["macro"] = args.macro if args.macro is not None else (MACRO_C3 if args.workload == "c3" else MACRO)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_c4(args)
+    elif args.workload == "schemes":
+        run_schemes(args)
+    elif args.workload == "c5":
+        _SIZE["macro"] = args.macro if args.macro is not None else 8
+        args.macro = _SIZE["macro"]
+        run_c5(args)
     else:
         run_gpu(args)
 

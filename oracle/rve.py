@@ -242,8 +242,19 @@ class PeriodicRVE:
         Abar = Am.reshape(d * d, d * d) - (L.T @ X) / self.volume
         return Abar.reshape(d, d, d, d)
 
-    def solve(self, Fbar, w0=None, rtol=1e-10, atol=1e-14, max_iter=30, max_steps=None, tangent=True):
-        """Full RVE solve: Newton, then Pbar, Wbar, <F> and (optionally) Abar."""
+    def solve(self, Fbar, w0=None, rtol=1e-10, atol=1e-14, max_iter=30, max_steps=None, tangent=True, stages=1):
+        """Full RVE solve: Newton, then Pbar, Wbar, <F> and (optionally) Abar.
+
+        stages > 1: load continuation from w = 0 (w0 is ignored); Newton solves at
+        I + (k/stages)(Fbar - I), k = 1 .. stages, each starting from the previous solution."""
+        Fbar = np.asarray(Fbar, dtype=np.float64)
+        if stages > 1:
+            I = np.eye(self.d)
+            w0 = np.zeros(self.n_dof)
+            for k in range(1, stages):
+                w0, status, _, hist = self.newton(I + (k / stages) * (Fbar - I), w0, rtol, atol, max_iter, max_steps)
+                if status not in (STATUS_OK, STATUS_NEWTON_CAP):
+                    return {"w": w0, "status": status, "newton_iters": 0, "history": hist}
         w, status, it, hist = self.newton(Fbar, w0, rtol, atol, max_iter, max_steps)
         out = {"w": w, "status": status, "newton_iters": it, "history": hist}
         if status in (STATUS_OK, STATUS_NEWTON_CAP):

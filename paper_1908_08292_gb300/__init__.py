@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("precision", ctypes.c_int),
                 ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("max_newton", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("max_cg", ctypes.c_int),
-                ("cond_rtol", ctypes.c_double), ("max_cond_cg", ctypes.c_int)]
+                ("cond_rtol", ctypes.c_double), ("max_cond_cg", ctypes.c_int),
+                ("retry_stages", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

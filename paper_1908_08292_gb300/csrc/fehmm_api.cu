@@ -78,7 +78,7 @@ int dupload(T*& dst, const T* src, size_t count) {
 bool valid_options(const fehmm_options* o) {
   return o && (o->dim == 2 || o->dim == 3) && (o->precision == FEHMM_PREC_FP64 || o->precision == FEHMM_PREC_MIXED) &&
          o->newton_rtol >= 0 && o->newton_atol >= 0 && o->max_newton >= 0 && o->cg_rtol > 0 && o->max_cg > 0 &&
-         o->cond_rtol > 0 && o->max_cond_cg > 0;
+         o->cond_rtol > 0 && o->max_cond_cg > 0 && o->retry_stages >= 0 && o->retry_stages <= 64;
 }
 
 }  // namespace
@@ -97,6 +97,7 @@ int fehmm_default_options(fehmm_options* opt, int dim, int precision) {
   opt->max_cg = 2000;
   opt->cond_rtol = precision == FEHMM_PREC_FP64 ? 1e-9 : 1e-6;
   opt->max_cond_cg = 4000;
+  opt->retry_stages = dim == 3 ? 4 : 0;
   return FEHMM_OK;
 }
 
@@ -315,6 +316,7 @@ static int rve_solve_impl(fehmm_ctx* c, const double* F, double* P, double* A, d
   a.max_newton = c->opt.max_newton;
   a.max_cg = c->opt.max_cg;
   a.max_cond_cg = c->opt.max_cond_cg;
+  a.retry_stages = c->opt.retry_stages;
   a.flags = flags;
   if (cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;
   const int blocks = std::min(c->n_qp, c->num_sms);

@@ -113,6 +113,7 @@ extern "C" int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_pe
   a.max_newton = opt->max_newton;
   a.max_cg = opt->max_cg;
   a.max_cond_cg = opt->max_cond_cg;
+  a.retry_stages = 0;
   a.flags = A ? 0 : kFlagNoTangent;
   // the shared work counter keeps the previous call's value: clear it on this stream
   if (cudaMemsetAsync(slots.queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;

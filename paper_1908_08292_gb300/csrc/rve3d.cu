@@ -623,74 +623,98 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
   for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) w[v] = v < 3 ? 0.0 : w_in[v];
   __syncthreads();
 
-  int status = kStatusNewtonCap, it = 0, cg_total = 0, nhalf = 0;
-  double r0 = 0.0, step = 1.0, Psum[9];
+  // Load continuation on failure: a Newton solve that ends in J <= 0, a non-finite residual or a
+  // PCG breakdown is restarted from w = 0 and Fbar is reached in retry_stages equal increments
+  // of Fbar - I, each increment a Newton solve warm-started from the previous one.
+  int status = kStatusNewtonCap, it_total = 0, cg_total = 0, stages = 1, stage = 1;
+  double Psum[9];
   for (;;) {
-    double bad = 0.0;
+    int it = 0, nhalf = 0;
+    double r0 = 0.0, step = 1.0;
+    status = kStatusNewtonCap;
+    for (;;) {
+      double bad = 0.0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Psum[k] = 0.0;
-    residual3(c, w, Psum, bad);
-    __syncthreads();
-    double rr = 0.0;
-    for (int v = threadIdx.x; v < NN; v += blockDim.x) {
-      double R[3];
-      gather_R(c, v, R);
-      if (v == 0) R[0] = R[1] = R[2] = 0.0;
+      for (int k = 0; k < 9; ++k) Psum[k] = 0.0;
+      residual3(c, w, Psum, bad);
+      __syncthreads();
+      double rr = 0.0;
+      for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+        double R[3];
+        gather_R(c, v, R);
+        if (v == 0) R[0] = R[1] = R[2] = 0.0;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        rr += R[d] * R[d];
-        c.sc.r[d * NN + v] = (TA)(-R[d]);  // right-hand side of the Newton correction
+        for (int d = 0; d < 3; ++d) {
+          rr += R[d] * R[d];
+          c.sc.r[d * NN + v] = (TA)(-R[d]);  // right-hand side of the Newton correction
+        }
       }
-    }
-    double v2[2] = {rr, bad};
-    block_sum_n<double>(v2, 2, c.red);
-    const double rn = sqrt(v2[0]);
-    if (it == 0) r0 = rn;
-    if ((v2[1] > 0.0 || !isfinite(rn)) && it > 0 && nhalf < kMaxStepHalvings) {
-      // backtrack: w = w_prev + step x  ->  w_prev + (step/2) x
-      ++nhalf;
-      step *= 0.5;
+      double v2[2] = {rr, bad};
+      block_sum_n<double>(v2, 2, c.red);
+      const double rn = sqrt(v2[0]);
+      if (it == 0) r0 = rn;
+      if ((v2[1] > 0.0 || !isfinite(rn)) && it > 0 && nhalf < kMaxStepHalvings) {
+        // backtrack: w = w_prev + step x  ->  w_prev + (step/2) x
+        ++nhalf;
+        step *= 0.5;
+        for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+          if (v == 0) continue;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) w[3 * v + d] -= step * (double)c.sc.x[d * NN + v];
+        }
+        __syncthreads();
+        continue;
+      }
+      if (v2[1] > 0.0) {
+        status = kStatusJNonPos;
+        break;
+      }
+      if (!isfinite(rn)) {
+        status = kStatusNonFinite;
+        break;
+      }
+      if (rn <= fmax(a.newton_rtol * r0, a.newton_atol)) {
+        status = kStatusOk;
+        break;
+      }
+      if (it >= a.max_newton) {
+        status = kStatusNewtonCap;
+        break;
+      }
+      tangent3<TA, false>(c, w, nullptr);
+      int pst = kStatusOk;
+      cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
+      if (pst == kStatusPcgBreakdown) {
+        status = kStatusPcgBreakdown;
+        break;
+      }
+      step = 1.0;
+      nhalf = 0;
       for (int v = threadIdx.x; v < NN; v += blockDim.x) {
         if (v == 0) continue;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) w[3 * v + d] -= step * (double)c.sc.x[d * NN + v];
+        for (int d = 0; d < 3; ++d) w[3 * v + d] += (double)c.sc.x[d * NN + v];
       }
       __syncthreads();
-      continue;
+      ++it;
     }
-    if (v2[1] > 0.0) {
-      status = kStatusJNonPos;
+    it_total += it;
+    const bool failed = !(status == kStatusOk || status == kStatusNewtonCap);
+    if (failed && stages == 1 && a.retry_stages > 1) {
+      stages = a.retry_stages;
+      stage = 0;
+      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) w[v] = 0.0;
+    } else if (failed || stage >= stages) {
       break;
     }
-    if (!isfinite(rn)) {
-      status = kStatusNonFinite;
-      break;
-    }
-    if (rn <= fmax(a.newton_rtol * r0, a.newton_atol)) {
-      status = kStatusOk;
-      break;
-    }
-    if (it >= a.max_newton) {
-      status = kStatusNewtonCap;
-      break;
-    }
-    tangent3<TA, false>(c, w, nullptr);
-    int pst = kStatusOk;
-    cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
-    if (pst == kStatusPcgBreakdown) {
-      status = kStatusPcgBreakdown;
-      break;
-    }
-    step = 1.0;
-    nhalf = 0;
-    for (int v = threadIdx.x; v < NN; v += blockDim.x) {
-      if (v == 0) continue;
+    ++stage;
+    const double* Ft = a.F + (size_t)qp * 9;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) w[3 * v + d] += (double)c.sc.x[d * NN + v];
-    }
+    for (int k = 0; k < 9; ++k)
+      c.Fb[k] = stage == stages ? Ft[k] : (k % 4 == 0 ? 1.0 : 0.0) + (Ft[k] - (k % 4 == 0 ? 1.0 : 0.0)) * stage / stages;
     __syncthreads();
-    ++it;
   }
+  const int it = it_total;
 
   const bool usable = (status == kStatusOk || status == kStatusNewtonCap);
   double Pv[10];

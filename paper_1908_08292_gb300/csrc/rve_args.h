@@ -28,6 +28,7 @@ struct Rve2dArgs {
   void* scratch;                // per-block global scratch (FP64 mode)
   double newton_rtol, newton_atol, cg_rtol, cond_rtol;
   int max_newton, max_cg, max_cond_cg, flags;
+  int retry_stages;      // > 1: load continuation from w = 0 after a failed Newton solve
   const int32_t* n_dev;  // optional: number of work items in device memory (order = a qp list)
   int fixed_n;        // fixed-layout launches only: grid size of every RVE
   int phase_per_qp;   // fixed-layout launches only: 1 = one phase map per qp, 0 = one shared

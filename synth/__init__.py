@@ -147,10 +147,14 @@ def config1() -> Problem:
                    np.zeros(64, dtype=np.int64), dofs, vals, 10, "fp64", 1e-10)
 
 
-def config2(macro: int = 32, rve: int = 32, seed: int = 1002, n_rve: int | None = None) -> Problem:
-    """2D batch: macro macro x macro Q1 (4 qps/element, one RVE each) of rve x rve RVEs,
-    random circle (centre uniform, r ~ U(0.15, 0.35)), stiffness ratio log-uniform in [5, 50]."""
-    n_qp = macro * macro * 4
+def config2(macro: int = 32, rve: int = 32, seed: int = 1002, n_rve: int | None = None,
+            macro_y: int | None = None) -> Problem:
+    """2D batch: macro macro x macro_y (default square) Q1 on the unit square (4 qps/element, one
+    RVE each) of rve x rve RVEs, random circle (centre uniform, r ~ U(0.15, 0.35)), stiffness
+    ratio log-uniform in [5, 50].  A taller mesh (macro_y = k macro) keeps the first RVEs of the
+    square workload and adds k - 1 times as many (weak scaling over k ranks)."""
+    macro_y = macro if macro_y is None else macro_y
+    n_qp = macro * macro_y * 4
     n_rve = n_qp if n_rve is None else n_rve
     u = uniform(seed, np.arange(n_rve), 4)
     centers = u[:, 0:2]
@@ -160,10 +164,10 @@ def config2(macro: int = 32, rve: int = 32, seed: int = 1002, n_rve: int | None 
     E = np.stack([np.ones(n_rve), ratio], axis=1)
     nu = np.full((n_rve, 2), 0.3)
     F_end = [[1.3, 0.3], [0.0, 1.3]]
-    dofs, vals = _affine_bc((macro, macro), F_end,
+    dofs, vals = _affine_bc((macro, macro_y), F_end,
                             lambda X: np.isclose(X, 0.0).any(1) | np.isclose(X, 1.0).any(1))
     qp_rve = np.arange(n_qp) % n_rve
-    return Problem(f"c2_2d_mixed_{macro}x{macro}_rve{rve}", 2, (macro, macro),
+    return Problem(f"c2_2d_mixed_{macro}x{macro_y}_rve{rve}", 2, (macro, macro_y),
                    np.full(n_rve, rve), phases, E, nu, qp_rve, dofs, vals, 20, "mixed", 1e-10,
                    extra={"centers": centers, "radii": radii, "ratio": ratio, "F_end": np.array(F_end)})
 

@@ -68,3 +68,25 @@ def test_homogeneous_rve_is_pointwise_law_3d():
         assert out["status"][q] == 0 and out["iters"][q][0] == 0
         np.testing.assert_allclose(out["P"][q], mat.P_of_F(Fs[q], lam, mu), atol=1e-13)
         np.testing.assert_allclose(out["A"][q], mat.A_of_F(Fs[q], lam, mu), atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_failed_start_retried_by_load_continuation(precision):
+    """A start fluctuation that folds elements (J <= 0 before the first Newton step) fails with
+    retry_stages = 0 and, with retry_stages = 4, is re-solved from zero by load continuation to
+    the oracle's continuation result (which equals the direct solve from zero)."""
+    n = 4
+    phase = synth.phase_from_inclusions(n, 3, [[0.45, 0.5, 0.55]], [0.3])
+    E, nu = [1.0, 10.0], [0.3, 0.25]
+    F = synth.random_F(611, 1, 3, 0.2)
+    w_bad = np.zeros(3 * n ** 3)
+    w_bad[3] = 0.8  # x-displacement of node 1: dw_x/dX_1 about -3 in the next elements
+    rve = PeriodicRVE(n, 3, phase, E, nu)
+    assert rve.newton(F[0], w_bad)[1] == 2  # the start state is inadmissible (J <= 0)
+    opts = dict(STRICT) if precision == "fp64" else {}
+    off = gpu_batch(3, precision, [n], [phase], [E], [nu], [0], F, w0=[w_bad], retry_stages=0, **opts)
+    assert off["status"][0] == 2
+    on = gpu_batch(3, precision, [n], [phase], [E], [nu], [0], F, w0=[w_bad], retry_stages=4, **opts)
+    ref = rve.solve(F[0], rtol=1e-14, atol=1e-16, stages=4)
+    check(on, [ref], TOL[precision])
+    assert on["iters"][0][0] > 4  # Newton iterations summed over the first try and the four increments
