@@ -89,12 +89,13 @@ typedef struct {
   int max_cg;
   double cond_rtol;     /* relative tolerance of the PCG solves of the tangent transfer */
   int max_cond_cg;
-  int retry_stages;     /* 3D only (0..64, default 4; ignored in 2D): a point whose Newton solve
-                           ends in FEHMM_RVE_J_NONPOS, FEHMM_RVE_NONFINITE or
-                           FEHMM_RVE_PCG_BREAKDOWN is solved again from zero fluctuations,
-                           reaching Fbar in retry_stages equal increments of Fbar - I (load
-                           continuation, each increment warm-started from the last); 0 or 1
-                           turns the retry off.  Its status is that of the retried solve. */
+  int retry_stages;     /* 0..64, default 4: a point whose Newton solve ends in
+                           FEHMM_RVE_J_NONPOS, FEHMM_RVE_NONFINITE or FEHMM_RVE_PCG_BREAKDOWN is
+                           solved again from zero fluctuations, reaching Fbar in retry_stages
+                           equal increments of Fbar - I (load continuation, each increment
+                           warm-started from the last, each allowed max(max_newton, 25)
+                           Newton iterations); 0 or 1 turns the retry off.  The status is that
+                           of the retried solve; the Newton count adds up all stages. */
 } fehmm_options;
 
 /* Fill `opt` with defaults for dim (2|3) and precision. */

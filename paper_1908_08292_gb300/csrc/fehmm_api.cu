@@ -97,7 +97,7 @@ int fehmm_default_options(fehmm_options* opt, int dim, int precision) {
   opt->max_cg = 2000;
   opt->cond_rtol = precision == FEHMM_PREC_FP64 ? 1e-9 : 1e-6;
   opt->max_cond_cg = 4000;
-  opt->retry_stages = dim == 3 ? 4 : 0;
+  opt->retry_stages = 4;
   return FEHMM_OK;
 }
 
@@ -525,7 +525,7 @@ int fehmm_macro_solve(fehmm_ctx* c, const double* K_vals, const double* f, doubl
   a.out = info;
   a.rtol = rtol;
   a.max_it = max_it;
-  if (macro_solve_launch(a, macro_solve_blocks(c->num_sms, c->macro_nnz), (cudaStream_t)stream) != cudaSuccess) {
+  if (macro_solve_launch(a, macro_solve_blocks(c->num_sms, c->macro_rows), (cudaStream_t)stream) != cudaSuccess) {
     cudaGetLastError();
     return FEHMM_ERR_CUDA;
   }

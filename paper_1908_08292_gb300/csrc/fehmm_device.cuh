@@ -25,6 +25,9 @@ constexpr int kFlagNoTangent = 1, kFlagFromCommitted = 2, kFlagEnergy = 4;
 // Newton globalisation: after an update that makes det F <= 0 somewhere (or the residual
 // non-finite) the step is halved, up to this many times, before the RVE is reported failed.
 constexpr int kMaxStepHalvings = 8;
+// Newton cap of each load-continuation stage of a retried solve (at least max_newton): a retry
+// recovers a usable state even when max_newton = 1 (the alternating scheme).
+constexpr int kRetryNewtonCap = 25;
 
 template <typename T> struct vec2_of;
 template <> struct vec2_of<float> { using type = float2; };

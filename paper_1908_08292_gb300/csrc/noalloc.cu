@@ -83,7 +83,7 @@ extern "C" int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_pe
   if (grid_n < 2 || (grid_n % 2) != 0) return FEHMM_ERR_ARG;
   if (grid_n * grid_n > kNoallocMaxNN) return FEHMM_ERR_TOO_LARGE;
   if (!(opt->cg_rtol > 0) || !(opt->cond_rtol > 0) || opt->max_cg <= 0 || opt->max_cond_cg <= 0 ||
-      opt->max_newton < 0)
+      opt->max_newton < 0 || opt->retry_stages < 0 || opt->retry_stages > 64)
     return FEHMM_ERR_ARG;
   DeviceSlots slots;
   int rc = device_slots(&slots);
@@ -113,7 +113,7 @@ extern "C" int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_pe
   a.max_newton = opt->max_newton;
   a.max_cg = opt->max_cg;
   a.max_cond_cg = opt->max_cond_cg;
-  a.retry_stages = 0;
+  a.retry_stages = opt->retry_stages;
   a.flags = A ? 0 : kFlagNoTangent;
   // the shared work counter keeps the previous call's value: clear it on this stream
   if (cudaMemsetAsync(slots.queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;

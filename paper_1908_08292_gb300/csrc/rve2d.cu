@@ -708,14 +708,9 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   const size_t w_off = kFixed ? (size_t)qp * 2 * n * n : (size_t)a.qp_w_off[qp];
   const double* w_in = a.w_in + w_off;
   double* w_out = a.w_out + w_off;
-  double Fbd[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Fbd[k] = a.F[(size_t)qp * 4 + k];
-  TA Fb[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Fb[k] = (TA)Fbd[k];
+  // Fbar of the current continuation stage, in shared memory (misc[0..3]); read where used
+  if (tid < 4) sm.misc[tid] = a.F[(size_t)qp * 4 + tid];
   if (tid < 2 * kMaxPhase) sm.lame[tid] = a.rve_lame[(size_t)rv * 2 * kMaxPhase + tid];
-  if (tid < 4) sm.misc[tid] = Fbd[tid];
   for (int v = tid; v < NN; v += blockDim.x) {
     double2 wv = make_double2(w_in[2 * v], w_in[2 * v + 1]);
     if (v == 0) wv = make_double2(0.0, 0.0);
@@ -735,101 +730,146 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   vec2_t<TA>* Lb = Xs + 4 * NN;                               // [4][NN]
   TA Minv[2][4];
 
-  int status = kStatusNewtonCap, it = 0, cg_total = 0, nhalf = 0;
-  double r0 = 0.0, step = 1.0;
+  // Load continuation on failure (as in the 3D kernel): a Newton solve ending in J <= 0, a
+  // non-finite residual or a PCG breakdown restarts from w = 0 and reaches Fbar in retry_stages
+  // equal increments of Fbar - I.
+  // The stage counters live in shared memory (block-uniform) to keep them out of the registers
+  // of the PCG loop.
+  __shared__ int s_ctl[3];  // stages, stage, Newton iterations of the earlier stages
+  if (tid == 0) {
+    s_ctl[0] = 1;
+    s_ctl[1] = 1;
+    s_ctl[2] = 0;
+  }
+  __syncthreads();
+  int status = kStatusNewtonCap, it = 0, cg_total = 0;
   double Psum[4];
   for (;;) {
-    // ---- FP64 residual
-    Psum[0] = Psum[1] = Psum[2] = Psum[3] = 0.0;
-    double bad = 0.0;
-    if (o.active) {
+    int nhalf = 0;
+    double r0 = 0.0, step = 1.0;
+    it = 0;
+    status = kStatusNewtonCap;
+    for (;;) {
+      // ---- FP64 residual
+      Psum[0] = Psum[1] = Psum[2] = Psum[3] = 0.0;
+      double bad = 0.0;
+      if (o.active) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int e = o.node[s];
-        const int ph = phase[e];
-        element_residual(e, n, sm.w, Fbd, sm.lame[2 * ph], sm.lame[2 * ph + 1], stage_f, Psum, bad);
+        for (int s = 0; s < 2; ++s) {
+          const int e = o.node[s];
+          const int ph = phase[e];
+          element_residual(e, n, sm.w, sm.misc, sm.lame[2 * ph], sm.lame[2 * ph + 1], stage_f, Psum, bad);
+        }
       }
-    }
-    __syncthreads();
-    double R[4] = {0, 0, 0, 0};
-    if (o.active) {
+      __syncthreads();
+      double R[4] = {0, 0, 0, 0};
+      if (o.active) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int nd = o.node[s], i = nd % n, j = nd / n;
-        const int im = (i - 1 + n) % n, jm = (j - 1 + n) % n;
-        const int eA = nd, eB = im + n * j, eC = im + n * jm, eD = i + n * jm;
-        R[2 * s] = stage_f[0 * NN + eA] + stage_f[2 * NN + eB] + stage_f[4 * NN + eC] + stage_f[6 * NN + eD];
-        R[2 * s + 1] = stage_f[1 * NN + eA] + stage_f[3 * NN + eB] + stage_f[5 * NN + eC] + stage_f[7 * NN + eD];
+        for (int s = 0; s < 2; ++s) {
+          const int nd = o.node[s], i = nd % n, j = nd / n;
+          const int im = (i - 1 + n) % n, jm = (j - 1 + n) % n;
+          const int eA = nd, eB = im + n * j, eC = im + n * jm, eD = i + n * jm;
+          R[2 * s] = stage_f[0 * NN + eA] + stage_f[2 * NN + eB] + stage_f[4 * NN + eC] + stage_f[6 * NN + eD];
+          R[2 * s + 1] = stage_f[1 * NN + eA] + stage_f[3 * NN + eB] + stage_f[5 * NN + eC] + stage_f[7 * NN + eD];
+        }
+        if (o.node[0] == 0) R[0] = R[1] = 0.0;
       }
-      if (o.node[0] == 0) R[0] = R[1] = 0.0;
-    }
-    double v2[2] = {R[0] * R[0] + R[1] * R[1] + R[2] * R[2] + R[3] * R[3], bad};
-    block_sum<2, double>(v2, sm.red + (it & 1) * 512);
-    const double rn = sqrt(v2[0]);
-    if (it == 0) r0 = rn;
-    if ((v2[1] > 0.0 || !isfinite(rn)) && it > 0 && nhalf < kMaxStepHalvings) {
-      // backtrack: w = w_prev + step x  ->  w_prev + (step/2) x
-      ++nhalf;
-      step *= 0.5;
+      double v2[2] = {R[0] * R[0] + R[1] * R[1] + R[2] * R[2] + R[3] * R[3], bad};
+      block_sum<2, double>(v2, sm.red + (it & 1) * 512);
+      const double rn = sqrt(v2[0]);
+      if (it == 0) r0 = rn;
+      if ((v2[1] > 0.0 || !isfinite(rn)) && it > 0 && nhalf < kMaxStepHalvings) {
+        // backtrack: w = w_prev + step x  ->  w_prev + (step/2) x
+        ++nhalf;
+        step *= 0.5;
+        if (o.active) {
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const int nd = o.node[s];
+            double2 wv = sm.w[nd];
+            const vec2_t<TA> dx = sm.x[nd];
+            wv.x -= step * (double)dx.x;
+            wv.y -= step * (double)dx.y;
+            sm.w[nd] = wv;
+            if constexpr (REG) sm.w32[nd] = make_float2((float)wv.x, (float)wv.y);
+          }
+        }
+        __syncthreads();
+        continue;
+      }
+      if (v2[1] > 0.0) {
+        status = kStatusJNonPos;
+        break;
+      }
+      if (!isfinite(rn)) {
+        status = kStatusNonFinite;
+        break;
+      }
+      if (rn <= fmax(a.newton_rtol * r0, a.newton_atol)) {
+        status = kStatusOk;
+        break;
+      }
+      if (it >= (s_ctl[0] > 1 ? max(a.max_newton, kRetryNewtonCap) : a.max_newton)) {
+        status = kStatusNewtonCap;
+        break;
+      }
+      // ---- tangent and PCG correction
+      {
+        const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
+        build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb);
+      }
+      TA b[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) b[k] = (TA)(-R[k]);
+      int pst = kStatusOk;
+      cg_total += pcg_pair<TA, REG>(S, o, Minv, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redA, redB, &pst, true);
+      if (pst == kStatusPcgBreakdown) {
+        status = kStatusPcgBreakdown;
+        break;
+      }
+      step = 1.0;
+      nhalf = 0;
       if (o.active) {
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           const int nd = o.node[s];
           double2 wv = sm.w[nd];
           const vec2_t<TA> dx = sm.x[nd];
-          wv.x -= step * (double)dx.x;
-          wv.y -= step * (double)dx.y;
+          wv.x += (double)dx.x;
+          wv.y += (double)dx.y;
           sm.w[nd] = wv;
           if constexpr (REG) sm.w32[nd] = make_float2((float)wv.x, (float)wv.y);
         }
       }
       __syncthreads();
-      continue;
+      ++it;
     }
-    if (v2[1] > 0.0) {
-      status = kStatusJNonPos;
-      break;
-    }
-    if (!isfinite(rn)) {
-      status = kStatusNonFinite;
-      break;
-    }
-    if (rn <= fmax(a.newton_rtol * r0, a.newton_atol)) {
-      status = kStatusOk;
-      break;
-    }
-    if (it >= a.max_newton) {
-      status = kStatusNewtonCap;
-      break;
-    }
-    // ---- tangent and PCG correction
-    build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb);
-    TA b[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) b[k] = (TA)(-R[k]);
-    int pst = kStatusOk;
-    cg_total += pcg_pair<TA, REG>(S, o, Minv, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redA, redB, &pst, true);
-    if (pst == kStatusPcgBreakdown) {
-      status = kStatusPcgBreakdown;
-      break;
-    }
-    step = 1.0;
-    nhalf = 0;
-    if (o.active) {
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int nd = o.node[s];
-        double2 wv = sm.w[nd];
-        const vec2_t<TA> dx = sm.x[nd];
-        wv.x += (double)dx.x;
-        wv.y += (double)dx.y;
-        sm.w[nd] = wv;
-        if constexpr (REG) sm.w32[nd] = make_float2((float)wv.x, (float)wv.y);
+    const bool failed = !(status == kStatusOk || status == kStatusNewtonCap);
+    int stages = s_ctl[0], stage = s_ctl[1];
+    if (failed && stages == 1 && a.retry_stages > 1) {
+      stages = a.retry_stages;
+      stage = 0;
+      for (int v = tid; v < NN; v += blockDim.x) {
+        sm.w[v] = make_double2(0.0, 0.0);
+        if constexpr (REG) sm.w32[v] = make_float2(0.f, 0.f);
       }
+    } else if (failed || stage >= stages) {
+      break;
+    }
+    ++stage;
+    __syncthreads();  // every thread has read s_ctl and finished with this stage's Fbar
+    if (tid < 4) {
+      const double Ft = a.F[(size_t)qp * 4 + tid], id = (tid == 0 || tid == 3) ? 1.0 : 0.0;
+      sm.misc[tid] = stage == stages ? Ft : id + (Ft - id) * stage / stages;
+    }
+    if (tid == 0) {
+      s_ctl[0] = stages;
+      s_ctl[1] = stage;
+      s_ctl[2] += it;
     }
     __syncthreads();
-    ++it;
   }
+  const int it_total = s_ctl[2] + it;
 
   // ---- homogenised stress (and energy) at the final state
   double Pv[5] = {Psum[0], Psum[1], Psum[2], Psum[3], 0.0};
@@ -840,7 +880,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
     for (int s = 0; s < 2; ++s) {
       const int e = o.node[s];
       const int ph = phase[e];
-      Pv[4] += element_energy(e, n, sm.w, Fbd, sm.lame[2 * ph], sm.lame[2 * ph + 1]);
+      Pv[4] += element_energy(e, n, sm.w, sm.misc, sm.lame[2 * ph], sm.lame[2 * ph + 1]);
     }
   }
   // the last residual norm used buffer (it & 1) and may still be read: use the other one
@@ -855,6 +895,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   double Q[10];
   const bool want_A = usable && !(a.flags & kFlagNoTangent) && a.A != nullptr;
   if (want_A) {
+    const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
     build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb);
     vec2_t<TA>* X = Xs;
     for (int c = 0; c < 4; ++c) {
@@ -902,7 +943,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   if (tid == 0) {
     a.status[qp] = status;
     if (a.iters) {
-      a.iters[(size_t)qp * 4 + 0] = it;
+      a.iters[(size_t)qp * 4 + 0] = it_total;
       a.iters[(size_t)qp * 4 + 1] = cg_total;
       a.iters[(size_t)qp * 4 + 2] = cond_total;
       a.iters[(size_t)qp * 4 + 3] = cond_max;

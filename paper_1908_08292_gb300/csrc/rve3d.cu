@@ -677,7 +677,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
         status = kStatusOk;
         break;
       }
-      if (it >= a.max_newton) {
+      if (it >= (stages > 1 ? max(a.max_newton, kRetryNewtonCap) : a.max_newton)) {
         status = kStatusNewtonCap;
         break;
       }

@@ -66,14 +66,14 @@ struct MacroSolveArgs {
   const double* f;          // macro residual
   const uint8_t* fixed;     // [n] 1 = Dirichlet dof
   double* du;               // [n] correction (output)
-  double* work;             // 5n + 2*blocks doubles
+  double* work;             // 6n + 2*blocks doubles
   double* out;              // [3]: |f_free|_2, iterations, status (0 ok, 1 cap, 2 breakdown)
   double rtol;
   int max_it;
 };
 
 size_t macro_solve_work_doubles(int n, int blocks);
-int macro_solve_blocks(int num_sms, long long nnz);
+int macro_solve_blocks(int num_sms, long long n_rows);
 cudaError_t macro_solve_launch(const MacroSolveArgs& a, int blocks, cudaStream_t stream);
 
 cudaError_t macro_qp_F_launch(const MacroArgs& m, cudaStream_t stream);

@@ -35,8 +35,7 @@ def test_default_options_and_argument_errors(L):
     opt = fe.Options()
     assert L.fehmm_default_options(ctypes.byref(opt), 2, fe.PREC_MIXED) == 0
     assert opt.dim == 2 and opt.precision == 1 and opt.max_newton > 0 and 0 < opt.cg_rtol < 1
-    assert opt.retry_stages == 0  # the load-continuation retry is a 3D option
-    assert L.fehmm_default_options(ctypes.byref(opt), 3, fe.PREC_MIXED) == 0 and opt.retry_stages == 4
+    assert opt.retry_stages == 4  # load-continuation retry of failed RVE solves, on by default
     assert L.fehmm_default_options(ctypes.byref(opt), 4, 0) == -1
     assert L.fehmm_default_options(None, 2, 0) == -1
     assert L.fehmm_create(None, None) == -1

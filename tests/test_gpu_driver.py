@@ -12,12 +12,14 @@ from oracle.macro import MacroMesh
 pytestmark = pytest.mark.gpu
 
 
-def test_macro_solve_matches_direct_solve():
+@pytest.mark.parametrize("n_el", [(6, 5), (52, 48)])
+def test_macro_solve_matches_direct_solve(n_el):
+    """(6, 5): 84 rows, 3 blocks; (52, 48): 5194 rows, every SM a block and several rows per
+    lane group."""
     import torch
 
     import paper_1908_08292_gb300 as fe
 
-    n_el = (6, 5)
     mesh = MacroMesh(n_el)
     lam, mu = mat.lame(3.0, 0.3)
     F = synth.random_F(501, mesh.n_qp, 2, 0.05)
@@ -36,7 +38,7 @@ def test_macro_solve_matches_direct_solve():
         du = torch.zeros(nr, dtype=torch.float64, device=dev)
         info = torch.zeros(3, dtype=torch.float64, device=dev)
         ctx.macro_assemble(Pt, At, f, K)
-        ctx.macro_solve(K, f, du, info, rtol=1e-13)
+        ctx.macro_solve(K, f, du, info, rtol=1e-13, max_it=20000)
         torch.cuda.synchronize()
         du, info = du.cpu().numpy(), info.cpu().numpy()
     free = np.setdiff1d(np.arange(mesh.n_dof), dofs)
@@ -44,7 +46,8 @@ def test_macro_solve_matches_direct_solve():
     ref[free] = spla.spsolve(K_ref[free][:, free].tocsc(), -f_ref[free])
     assert info[2] == 0
     assert abs(info[0] - np.linalg.norm(f_ref[free])) < 1e-12 * np.linalg.norm(f_ref)
-    np.testing.assert_allclose(du, ref, atol=1e-9 * np.abs(ref).max())
+    # CG error <= condition number x relative residual: about 1e4 x 1e-13 on the larger mesh
+    np.testing.assert_allclose(du, ref, atol=(1e-9 if mesh.n_dof < 1000 else 1e-8) * np.abs(ref).max())
     assert np.all(du[dofs] == 0)
 
 

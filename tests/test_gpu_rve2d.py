@@ -123,3 +123,25 @@ def test_warm_start_and_alternating_single_iteration():
     assert out1["iters"][0][0] == 1 and out1["status"][0] == 1  # cap after one step
     assert np.abs(out1["w"][0] - one["w"]).max() < 1e-11
     assert rel_err(out1["P"][0], one["P"], 1e-3) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_failed_start_retried_by_load_continuation(precision):
+    """A start fluctuation that folds elements (J <= 0 before the first Newton step) fails with
+    retry_stages = 0 and, with retry_stages = 4, is re-solved from zero by load continuation to
+    the oracle's continuation result."""
+    n = 8
+    phase = synth.phase_from_inclusions(n, 2, [[0.4, 0.55]], [0.3])
+    E, nu = [1.0, 10.0], [0.3, 0.3]
+    F = synth.random_F(121, 1, 2, 0.2)
+    w_bad = np.zeros(2 * n * n)
+    w_bad[2] = 0.8  # x-displacement of node 1: dw_x/dX_1 about -6 in the next elements
+    rve = PeriodicRVE(n, 2, phase, E, nu)
+    assert rve.newton(F[0], w_bad)[1] == 2  # the start state is inadmissible (J <= 0)
+    opts = dict(STRICT) if precision == "fp64" else dict(newton_rtol=1e-12, newton_atol=1e-15)
+    off = gpu_batch(2, precision, [n], [phase], [E], [nu], [0], F, w0=[w_bad], retry_stages=0, **opts)
+    assert off["status"][0] == 2
+    on = gpu_batch(2, precision, [n], [phase], [E], [nu], [0], F, w0=[w_bad], retry_stages=4, **opts)
+    ref = rve.solve(F[0], rtol=1e-14, atol=1e-16, stages=4)
+    check(on, [ref], TOL[precision])
+    assert on["iters"][0][0] > 4

@@ -133,28 +133,30 @@ def test_laminate_exact_solution(d):
             np.testing.assert_allclose(out["A"][:, :, k, l], fd, atol=2e-8)
 
 
-def bad_start_3d(n, amp=0.8):
+def bad_start(n, d, amp=0.8):
     """A fluctuation that folds the elements next to node 1 (dw_x/dX_1 about -amp*n near it)."""
-    w = np.zeros(3 * n ** 3)
-    w[3 * 1 + 0] = amp
+    w = np.zeros(d * n ** d)
+    w[d * 1 + 0] = amp
     return w
 
 
-def test_load_continuation_reaches_the_laminate_closed_form():
+@pytest.mark.parametrize("d", [2, 3])
+def test_load_continuation_reaches_the_laminate_closed_form(d):
     """Continuation from w = 0 in equal increments of Fbar - I lands on the exact laminate
-    solution (3D), from a start state the plain Newton iteration rejects (J <= 0)."""
+    solution, from a start state the plain Newton iteration rejects (J <= 0)."""
     from oracle.rve import STATUS_J_NONPOS
     n = 4
-    ph = (np.arange(n ** 3) // n ** 2 < 1).astype(np.uint8)
+    ph = (np.arange(n ** d) // n ** (d - 1) < 1).astype(np.uint8)
     E, nu = [1.0, 7.0], [0.3, 0.2]
-    rve = PeriodicRVE(n, 3, ph, E, nu)
+    rve = PeriodicRVE(n, d, ph, E, nu)
     lam, mu = mat.lame(np.array(E), np.array(nu))
-    Fbar = synth.random_F(29, 1, 3, 0.2)[0]
-    w_bad = bad_start_3d(n)
+    Fbar = synth.random_F(29, 1, d, 0.2)[0]
+    w_bad = bad_start(n, d)
     assert rve.newton(Fbar, w_bad)[1] == STATUS_J_NONPOS
     out = rve.solve(Fbar, w_bad, rtol=1e-14, stages=4)
     assert out["status"] == 0
-    N = np.array([0.0, 0.0, 1.0])
+    N = np.zeros(d)
+    N[-1] = 1.0
     np.testing.assert_allclose(out["P"], laminate_exact(Fbar, [1 - ph.mean(), ph.mean()], lam, mu, N), atol=5e-13)
     direct = rve.solve(Fbar, rtol=1e-14)
     np.testing.assert_allclose(out["A"], direct["A"], atol=1e-11)
