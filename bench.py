@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -35,8 +36,8 @@ UNIT = "RVE solves/s"
 MACRO, RVE_N, N_STEPS = 32, 32, 20
 MACRO_C3, N_STEPS_C3 = 8, 10
 
-# Algorithmic operation counts per unit of the 2D mixed kernel (derivation in the design doc,
-# counted from the kernel source, an FMA counting 2).
+# Algorithmic operation counts per unit of the 2D mixed kernel, counted from the kernel source
+# (an FMA counting 2).
 FP64_FLOP_PER_ELEMENT_RESIDUAL = 290.0   # F, J, F^-T, P and nodal forces at 4 Gauss points + gather
 FP32_FLOP_PER_ELEMENT_TANGENT = 1350.0   # 8x8 element tangent at 4 Gauss points + stencil gather
 FP32_FLOP_PER_NODE_PCG_ITER = 100.0      # 9-block 2x2 stencil apply + vector updates + 2 dots
@@ -84,11 +85,11 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="fehmm_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
