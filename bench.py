@@ -42,6 +42,13 @@ FP64_FLOP_PER_ELEMENT_RESIDUAL = 290.0   # F, J, F^-T, P and nodal forces at 4 G
 FP32_FLOP_PER_ELEMENT_TANGENT = 1350.0   # 8x8 element tangent at 4 Gauss points + stencil gather
 FP32_FLOP_PER_NODE_PCG_ITER = 100.0      # 9-block 2x2 stencil apply + vector updates + 2 dots
 FP32_FLOP_PER_ELEMENT_TRANSFER = 1500.0  # energy form of the tangent transfer (4 unit gradients)
+# multigrid preconditioner (2D, per fine node): V(1,1)-cycle per PCG iteration = two fine
+# applies (2 x 72), smoothing, residuals, restriction and prolongation (180 on the fine level,
+# 180/4 + 180/16 on the coarse levels, 2 for the coarsest 32 x 32 inverse apply); per tangent
+# build the Galerkin coarse element matrices (748 FMA per coarse element: 374 + 94 + 23 per fine
+# node), coarse stencils and the coarsest Gauss-Jordan inverse (2 x 32^3 / 1024)
+FP32_FLOP_PER_NODE_MG_ITER = 238.0
+FP32_FLOP_PER_NODE_MG_BUILD = 570.0
 FP64_FLOP_PER_ELEMENT_RESIDUAL_3D = 2640.0   # Hex8: 8 Gauss points x (grad, F^-T, P, nodal forces)
 FP32_FLOP_PER_ELEMENT_TANGENT_3D = 4200.0    # Gauss-point data + 3x3 diagonal blocks
 FP32_FLOP_PER_ELEMENT_APPLY_3D = 4000.0      # matrix-free apply: grad, dP = A:dF, nodal scatter
@@ -65,7 +72,9 @@ def workload_config(step_index):
                        f"E ratio log-U[5,50]), neo-Hookean, mixed FP32/FP64, macro iteration 1 of load step "
                        f"{step_index}/{N_STEPS} (biaxial 30% + shear 0.3)",
            "n_qp": MACRO * MACRO * W * 4, "rve_grid": RVE_N, "micro_dofs_per_rve": 2 * RVE_N * RVE_N,
-           "load_step": step_index, "l2": "flushed (256 MB write) between timed steps"}
+           "load_step": step_index, "l2": "flushed (256 MB write) between timed steps",
+           "rve_preconditioner": ("multigrid V(1,1), Galerkin levels 16/8/4" if _SIZE.get("precond", "mg") == "mg"
+                                  else "block-Jacobi")}
     if W > 1:
         cfg["parallelism"] = (f"dp{W}: macro elements in {W} contiguous blocks balanced by RVE dofs, one per rank; "
                               "all-reduce of f and K, macro solve on rank 0, broadcast of du")
@@ -168,14 +177,15 @@ def flops_3d(p, iters):
     return f64, f32
 
 
-def flops_2d(n, iters):
+def flops_2d(n, iters, mg=False):
     """FP64 and FP32 algorithmic flops of one RVE batch solve from the per-qp iteration counts."""
     el = n * n
     newton = iters[:, 0].astype(np.float64)
     cg = iters[:, 1].astype(np.float64) + iters[:, 2].astype(np.float64)
     f64 = ((newton + 1) * FP64_FLOP_PER_ELEMENT_RESIDUAL * el).sum()
-    f32 = ((newton + 1) * FP32_FLOP_PER_ELEMENT_TANGENT * el + cg * FP32_FLOP_PER_NODE_PCG_ITER * el
-           + FP32_FLOP_PER_ELEMENT_TRANSFER * el).sum()
+    per_iter = FP32_FLOP_PER_NODE_PCG_ITER + (FP32_FLOP_PER_NODE_MG_ITER if mg else 0.0)
+    per_build = FP32_FLOP_PER_ELEMENT_TANGENT + (FP32_FLOP_PER_NODE_MG_BUILD if mg else 0.0)
+    f32 = ((newton + 1) * per_build * el + cg * per_iter * el + FP32_FLOP_PER_ELEMENT_TRANSFER * el).sum()
     return f64, f32
 
 
@@ -195,6 +205,7 @@ def run_gpu(args):
     p, Fload = build_problem(args.step_index)
     n_qp = p.n_qp
     opts = {k: v for k, v in (("cg_rtol", args.cg_rtol), ("cond_rtol", args.cond_rtol)) if v is not None}
+    opts["precond"] = fe.PRECOND_MG if args.precond == "mg" else fe.PRECOND_JACOBI
     d = p.dim
     ctx = fe.Context(d, "mixed", **opts)
     ctx.add_rves(p.rve_n, p.rve_phase, p.rve_E, p.rve_nu)
@@ -319,7 +330,7 @@ def run_gpu(args):
     value = n_total / (t_step / args.steps)
     dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve[mine]], dtype=np.float64)
     dof_iter = float((dofs * iters[:, 0].astype(np.float64)).sum()) * world / (t_step / args.steps)
-    f64, f32 = flops_2d(RVE_N, iters) if d == 2 else flops_3d(p, iters)
+    f64, f32 = flops_2d(RVE_N, iters, args.precond == "mg") if d == 2 else flops_3d(p, iters)
     t_rve = statistics.mean(rve_ms) / 1e3
     ach_eq = (f32 + f64 * FP32_PEAK_TFLOPS / FP64_PEAK_TFLOPS) / t_rve / 1e12
     out = {
@@ -617,6 +628,8 @@ def main():
     ap.add_argument("--cg-rtol", type=float, default=None, help="override the Newton-correction PCG tolerance")
     ap.add_argument("--cond-rtol", type=float, default=None, help="override the tangent-transfer PCG tolerance")
     ap.add_argument("--macro", type=int, default=None, help="macro elements per axis (profiling runs use less)")
+    ap.add_argument("--precond", default="mg", choices=["mg", "jacobi"],
+                    help="RVE PCG preconditioner: multigrid V-cycle (default; 2D) or block-Jacobi")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "schemes"],
                     help="c2: 2D 4096 RVEs of 32x32 (default, the headline); c3: 3D 4096 uneven Hex8 RVEs; "
                          "c4: surrogate training; c5: surrogate+fallback vs plain macro iteration; "
@@ -630,6 +643,7 @@ def main():
     ap.add_argument("--c5-audit-stride", type=int, default=64)
     args = ap.parse_args()
     _SIZE["workload"] = args.workload
+    _SIZE["precond"] = args.precond
     _SIZE["macro"] = args.macro if args.macro is not None else (MACRO_C3 if args.workload == "c3" else MACRO)
     if args.impl == "reference":
         run_reference(args)

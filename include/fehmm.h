@@ -56,6 +56,9 @@ enum {
 
 enum { FEHMM_PREC_FP64 = 0, FEHMM_PREC_MIXED = 1 };
 
+/* Preconditioner of the RVE PCG solves (fehmm_options.precond). */
+enum { FEHMM_PRECOND_BLOCK_JACOBI = 0, FEHMM_PRECOND_MULTIGRID = 1 };
+
 /* Per-quadrature-point RVE status written by fehmm_rve_solve. */
 enum {
   FEHMM_RVE_OK = 0,            /* Newton converged */
@@ -96,6 +99,12 @@ typedef struct {
                            warm-started from the last, each allowed max(max_newton, 25)
                            Newton iterations); 0 or 1 turns the retry off.  The status is that
                            of the retried solve; the Newton count adds up all stages. */
+  int precond;          /* FEHMM_PRECOND_MULTIGRID (default): in 2D, grids n = 2^k m with
+                           m <= 4 and n >= 6 use a geometric V(1,1)-cycle with Galerkin
+                           coarse levels and block-Jacobi smoothing; other grids, 3D and
+                           FEHMM_PRECOND_BLOCK_JACOBI use block-Jacobi (inverted nodal d x d
+                           blocks).  The choice changes iteration counts, not the tolerances
+                           the solves meet. */
 } fehmm_options;
 
 /* Fill `opt` with defaults for dim (2|3) and precision. */

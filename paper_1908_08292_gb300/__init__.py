@@ -11,10 +11,11 @@ import os
 
 import numpy as np
 
-__all__ = ["Context", "FehmmError", "lib", "library_path", "PREC_FP64", "PREC_MIXED",
+__all__ = ["Context", "FehmmError", "lib", "library_path", "PREC_FP64", "PREC_MIXED", "PRECOND_JACOBI", "PRECOND_MG",
            "SOLVE_NO_TANGENT", "SOLVE_FROM_COMMITTED", "SOLVE_ENERGY", "RVE_STATUS"]
 
 PREC_FP64, PREC_MIXED = 0, 1
+PRECOND_JACOBI, PRECOND_MG = 0, 1
 SOLVE_NO_TANGENT, SOLVE_FROM_COMMITTED, SOLVE_ENERGY = 1, 2, 4
 RVE_STATUS = {0: "ok", 1: "newton_cap", 2: "J<=0", 3: "pcg_breakdown", 4: "nonfinite", 5: "pcg_cap"}
 
@@ -35,7 +36,7 @@ class Options(ctypes.Structure):
                 ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("max_newton", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("max_cg", ctypes.c_int),
                 ("cond_rtol", ctypes.c_double), ("max_cond_cg", ctypes.c_int),
-                ("retry_stages", ctypes.c_int)]
+                ("retry_stages", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -78,7 +78,8 @@ int dupload(T*& dst, const T* src, size_t count) {
 bool valid_options(const fehmm_options* o) {
   return o && (o->dim == 2 || o->dim == 3) && (o->precision == FEHMM_PREC_FP64 || o->precision == FEHMM_PREC_MIXED) &&
          o->newton_rtol >= 0 && o->newton_atol >= 0 && o->max_newton >= 0 && o->cg_rtol > 0 && o->max_cg > 0 &&
-         o->cond_rtol > 0 && o->max_cond_cg > 0 && o->retry_stages >= 0 && o->retry_stages <= 64;
+         o->cond_rtol > 0 && o->max_cond_cg > 0 && o->retry_stages >= 0 && o->retry_stages <= 64 &&
+         (o->precond == FEHMM_PRECOND_BLOCK_JACOBI || o->precond == FEHMM_PRECOND_MULTIGRID);
 }
 
 }  // namespace
@@ -98,6 +99,7 @@ int fehmm_default_options(fehmm_options* opt, int dim, int precision) {
   opt->cond_rtol = precision == FEHMM_PREC_FP64 ? 1e-9 : 1e-6;
   opt->max_cond_cg = 4000;
   opt->retry_stages = 4;
+  opt->precond = FEHMM_PRECOND_MULTIGRID;
   return FEHMM_OK;
 }
 
@@ -318,9 +320,11 @@ static int rve_solve_impl(fehmm_ctx* c, const double* F, double* P, double* A, d
   a.max_cond_cg = c->opt.max_cond_cg;
   a.retry_stages = c->opt.retry_stages;
   a.flags = flags;
+  const bool mixed = c->opt.precision == FEHMM_PREC_MIXED;
+  a.mg = c->opt.precond == FEHMM_PRECOND_MULTIGRID ? 1 : 0;
+  a.scratch_stride = c->opt.dim == 2 ? rve2d_scratch_stride(c->nn_max, mixed) : 0;
   if (cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;
   const int blocks = std::min(c->n_qp, c->num_sms);
-  const bool mixed = c->opt.precision == FEHMM_PREC_MIXED;
   const cudaError_t err = c->opt.dim == 2 ? rve2d_launch(a, mixed, blocks, s) : rve3d_launch(a, mixed, blocks, s);
   if (err != cudaSuccess) {
     cudaGetLastError();

@@ -114,6 +114,8 @@ extern "C" int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_pe
   a.max_cg = opt->max_cg;
   a.max_cond_cg = opt->max_cond_cg;
   a.retry_stages = opt->retry_stages;
+  a.mg = 0;  // block-Jacobi: the static scratch holds no multigrid levels
+  a.scratch_stride = 72LL * a.nn_max;
   a.flags = A ? 0 : kFlagNoTangent;
   // the shared work counter keeps the previous call's value: clear it on this stream
   if (cudaMemsetAsync(slots.queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;

@@ -51,6 +51,51 @@ __device__ __forceinline__ double gauss01(int g) {
   return g == 0 ? 0.21132486540518711775 : 0.78867513459481288225;
 }
 
+// Multigrid level counts and region sizes (the preconditioner itself is further below).
+constexpr float kMgOmega = 0.7f;
+constexpr int kMgMaxLevels = 4;  // coarse levels: 32 -> 16, 8, 4
+
+// Number of coarse levels (0: no multigrid for this grid).
+__host__ __device__ inline int mg_levels(int n) {
+  int l = 0, m = n;
+  while (m > 4 && (m & 1) == 0) {
+    m >>= 1;
+    ++l;
+  }
+  return (m <= 4 && l >= 1 && l <= kMgMaxLevels) ? l : 0;
+}
+
+// Element counts (TA) of the fast region (stencils, inverted blocks, vectors, coarsest inverse)
+// and of the slow region (coarse element matrices) for grid n.
+__host__ __device__ inline long long mg_fast_elems(int n) {
+  const int L = mg_levels(n);
+  if (!L) return 0;
+  long long e = 0;
+  for (int l = 1; l < L; ++l) {
+    const long long nn = (long long)(n >> l) * (n >> l);
+    e += 36 * nn + 4 * nn + 3 * 2 * nn;  // stencil, Minv, r/z/t
+  }
+  const long long nc = (long long)(n >> L) * (n >> L), D = 2 * nc;
+  return e + 2 * 2 * nc + D * (D + 1);  // r/z, inverse (row stride D + 1)
+}
+__host__ __device__ inline long long mg_slow_elems(int n) {
+  const int L = mg_levels(n);
+  long long e = 0;
+  for (int l = 1; l <= L; ++l) e += 36LL * (n >> l) * (n >> l);
+  return e;
+}
+// Largest region sizes over the grids a batch with n^2 <= nn_max may hold.
+__host__ __device__ inline long long mg_fast_max(int nn_max) {
+  long long m = 0;
+  for (int n = 2; n * n <= nn_max; n += 2) m = mg_fast_elems(n) > m ? mg_fast_elems(n) : m;
+  return m;
+}
+__host__ __device__ inline long long mg_slow_max(int nn_max) {
+  long long m = 0;
+  for (int n = 2; n * n <= nn_max; n += 2) m = mg_slow_elems(n) > m ? mg_slow_elems(n) : m;
+  return m;
+}
+
 template <typename TA>
 struct Smem2D {
   double2* w;        // [NN] fluctuation (FP64)
@@ -78,8 +123,14 @@ __host__ __device__ inline size_t smem2d_layout(int NN, Smem2D<TA>* s, unsigned 
   size_t o_x = take(sizeof(vec2_t<TA>) * NN);
   size_t stage_bytes = sizeof(double) * 8 * NN;                               // element forces
   if (REG && sizeof(float) * 36 * NN > stage_bytes) stage_bytes = sizeof(float) * 36 * NN;  // Ke
-  // condensation solutions X[4][NN] and right-hand sides L[4][NN]
+  // condensation solutions X[4][NN] and right-hand sides L[4][NN]; in mixed mode followed by
+  // the multigrid fast region of the RVE's grid (largest over the grids up to NN)
   if (sizeof(vec2_t<TA>) * 8 * NN > stage_bytes) stage_bytes = sizeof(vec2_t<TA>) * 8 * NN;
+  if (REG)
+    for (int m = 2; m * m <= NN; m += 2) {
+      const size_t need = sizeof(vec2_t<TA>) * 8 * (size_t)m * m + sizeof(TA) * (size_t)mg_fast_elems(m);
+      if (need > stage_bytes) stage_bytes = need;
+    }
   size_t o_stage = take(stage_bytes);
   size_t o_red = take(sizeof(double) * 2 * 512);
   size_t o_lame = take(sizeof(double) * 2 * kMaxPhase);
@@ -433,6 +484,338 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* buf) {
   b = (sb[0] + sb[1]) + (sb[2] + sb[3]);
 }
 
+template <typename TA>
+__device__ __forceinline__ void invert_block(const TA (&Kself)[4], bool pinned, TA (&Mi)[4]) {
+  const TA det = Kself[0] * Kself[3] - Kself[1] * Kself[2];
+  const TA id = pinned ? TA(0) : TA(1) / det;
+  Mi[0] = Kself[3] * id;
+  Mi[1] = -Kself[1] * id;
+  Mi[2] = -Kself[2] * id;
+  Mi[3] = Kself[0] * id;
+}
+
+// ------------------------------------------------------------------ multigrid preconditioner
+// Geometric V(1,1)-cycle over the periodic grid hierarchy n, n/2, ..., n_c (n_c <= 4), used as
+// the PCG preconditioner in place of block-Jacobi where n = 2^k m with m <= 4.
+//  * Galerkin coarse operators, built element by element: K_E = sum over the four fine elements
+//    e of the coarse element E of W_e^T K_e W_e, W_e the bilinear weights of E's corners at e's
+//    corners.  Bilinear prolongation P restricted to E depends only on E's corners, so the
+//    assembled K_E equal P^T K P exactly, and they are again element matrices, which gives the
+//    next level the same way.
+//  * The fine node 0 is pinned; the coarse node 0 (the same point) carries no basis function,
+//    so every level is pinned at node 0 and P^T K P stays the exact Galerkin operator.
+//  * Smoother: damped block-Jacobi (omega = 0.7) with the inverted nodal 2x2 blocks, one sweep
+//    before and one after the coarse correction (symmetric, so the V-cycle is an SPD
+//    preconditioner for CG).  Coarsest level (at most 16 nodes, 32 dofs): exact, through its
+//    dense inverse, computed by Gauss-Jordan elimination in one warp.
+//  * Fine level: the stencil of the PCG.  Coarse levels: stencil, inverted blocks and vectors
+//    in the fast region (shared memory in mixed mode, block scratch in FP64 mode); coarse
+//    element matrices (needed only while building) in the block's global scratch.
+template <typename TA>
+struct MgLevel {
+  int n, NN;
+  TA* st;          // [36][NN]
+  TA* mi;          // [4][NN]
+  vec2_t<TA>* r;   // [NN]
+  vec2_t<TA>* z;   // [NN]
+  vec2_t<TA>* t;   // [NN]
+  TA* ke;          // [36][NN] coarse element matrices (slow region)
+};
+
+template <typename TA>
+struct MgCtx {
+  int levels;  // coarse levels, 0 = off
+  int n;       // fine grid
+  TA* fast;
+  TA* slow;
+  // view of coarse level l (1..levels); the coarsest has no st/mi/t, its inverse follows r, z
+  __device__ __forceinline__ MgLevel<TA> level(int l) const {
+    MgLevel<TA> v;
+    TA* f = fast;
+    TA* k = slow;
+    for (int q = 1; q < l; ++q) {
+      const int nn = (n >> q) * (n >> q);
+      f += 46 * nn;
+      k += 36 * nn;
+    }
+    v.n = n >> l;
+    v.NN = v.n * v.n;
+    v.ke = k;
+    if (l < levels) {
+      v.st = f;
+      v.mi = f + 36 * v.NN;
+      v.r = reinterpret_cast<vec2_t<TA>*>(f + 40 * v.NN);
+      v.z = v.r + v.NN;
+      v.t = v.z + v.NN;
+    } else {
+      v.st = v.mi = nullptr;
+      v.r = reinterpret_cast<vec2_t<TA>*>(f);
+      v.z = v.r + v.NN;
+      v.t = nullptr;
+    }
+    return v;
+  }
+  __device__ __forceinline__ TA* coarsest_inverse() const {
+    const MgLevel<TA> v = level(levels);
+    return reinterpret_cast<TA*>(v.z + v.NN);
+  }
+};
+
+// Bilinear weight of coarse corner c at fine corner k of sub-element (a, b) of a coarse element.
+__host__ __device__ constexpr float mg_weight(int a, int b, int k, int c) {
+  const int x2 = a + offx(k), y2 = b + offy(k);  // position in halves of the coarse element
+  const float fx = offx(c) ? 0.5f * x2 : 1.0f - 0.5f * x2;
+  const float fy = offy(c) ? 0.5f * y2 : 1.0f - 0.5f * y2;
+  return fx * fy;
+}
+
+// Galerkin element matrix of coarse element E (grid nc = nf/2) from the four fine element
+// matrices in kf ([36][nf*nf], upper triangle of each 8x8).  The weights are compile-time
+// constants after unrolling, so the zero terms vanish (748 FMA per coarse element).
+template <typename TA>
+__device__ __forceinline__ void mg_coarse_element(const TA* kf, int nf, int E, TA* kc, int nnc) {
+  const int nc = nf >> 1, I = E % nc, J = E / nc, NNf = nf * nf;
+  TA acc[36];
+#pragma unroll
+  for (int q = 0; q < 36; ++q) acc[q] = TA(0);
+#pragma unroll
+  for (int ab = 0; ab < 4; ++ab) {
+    const int a = ab & 1, b = ab >> 1;
+    const int e = (2 * I + a) + nf * (2 * J + b);
+    TA k8[36];
+#pragma unroll
+    for (int q = 0; q < 36; ++q) k8[q] = kf[(size_t)q * NNf + e];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = r; c < 8; ++c) {
+        TA v = TA(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const float w = mg_weight(a, b, k, r >> 1) * mg_weight(a, b, m, c >> 1);
+            if (w != 0.0f) v += (TA)w * k8[tri8(2 * k + (r & 1), 2 * m + (c & 1))];
+          }
+        acc[tri8(r, c)] += v;
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < 36; ++q) kc[(size_t)q * nnc + E] = acc[q];
+}
+
+// y = K_l z at node v of a coarse level (zero at the pinned node).
+template <typename TA>
+__device__ __forceinline__ vec2_t<TA> mg_apply(const MgLevel<TA>& L, const vec2_t<TA>* z, int v) {
+  const int n = L.n, i = v % n, j = v / n;
+  TA yx = TA(0), yy = TA(0);
+#pragma unroll
+  for (int nb = 0; nb < 9; ++nb) {
+    const int dx = nb % 3 - 1, dy = nb / 3 - 1;
+    const vec2_t<TA> zn = z[(i + dx + n) % n + n * ((j + dy + n) % n)];
+    yx += L.st[(size_t)(nb * 4 + 0) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 1) * L.NN + v] * zn.y;
+    yy += L.st[(size_t)(nb * 4 + 2) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 3) * L.NN + v] * zn.y;
+  }
+  return v == 0 ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(yx, yy);
+}
+
+template <typename TA>
+__device__ __forceinline__ vec2_t<TA> mg_smooth(const TA* mi, int NN, int v, vec2_t<TA> r, TA omega) {
+  const TA m0 = mi[v], m1 = mi[NN + v], m2 = mi[2 * NN + v], m3 = mi[3 * NN + v];
+  return mk2<TA>(omega * (m0 * r.x + m1 * r.y), omega * (m2 * r.x + m3 * r.y));
+}
+
+// Full-weighting restriction (the transpose of bilinear prolongation) of the fine vector t
+// (grid nf) to coarse node I; zero at the pinned node.
+template <typename TA>
+__device__ __forceinline__ vec2_t<TA> mg_restrict(const vec2_t<TA>* t, int nf, int I) {
+  const int nc = nf >> 1, ix = 2 * (I % nc), jy = 2 * (I / nc);
+  TA sx = TA(0), sy = TA(0);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const TA wgt = TA((dx == 0 ? 1.0f : 0.5f) * (dy == 0 ? 1.0f : 0.5f));
+      const vec2_t<TA> v = t[(ix + dx + nf) % nf + nf * ((jy + dy + nf) % nf)];
+      sx += wgt * v.x;
+      sy += wgt * v.y;
+    }
+  return I == 0 ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(sx, sy);
+}
+
+// Bilinear prolongation of the coarse vector zc (grid nf/2) to fine node v of grid nf.
+template <typename TA>
+__device__ __forceinline__ vec2_t<TA> mg_prolong(const vec2_t<TA>* zc, int nf, int v) {
+  const int nc = nf >> 1, i = v % nf, j = v / nf;
+  const int i0 = i >> 1, j0 = j >> 1, i1 = (i0 + 1) % nc, j1 = (j0 + 1) % nc;
+  const vec2_t<TA> a = zc[i0 + nc * j0];
+  if (!(i & 1) && !(j & 1)) return a;
+  if (!(i & 1)) {  // between two coarse rows
+    const vec2_t<TA> c = zc[i0 + nc * j1];
+    return mk2<TA>(TA(0.5f) * (a.x + c.x), TA(0.5f) * (a.y + c.y));
+  }
+  const vec2_t<TA> b = zc[i1 + nc * j0];
+  if (!(j & 1)) return mk2<TA>(TA(0.5f) * (a.x + b.x), TA(0.5f) * (a.y + b.y));
+  const vec2_t<TA> c = zc[i0 + nc * j1], d = zc[i1 + nc * j1];
+  return mk2<TA>(TA(0.25f) * ((a.x + b.x) + (c.x + d.x)), TA(0.25f) * ((a.y + b.y) + (c.y + d.y)));
+}
+
+// Build the coarse levels below the fine element matrices kf0 (grid n, [36][n*n]).  Part 1 (the
+// Galerkin element matrices of every coarse level, slow region) runs while kf0 is intact and
+// before the fine stencil is gathered into registers, so its many live values do not compete
+// with the stencil; part 2 (coarse stencils, inverted blocks and the coarsest inverse, fast
+// region) runs after the fine gather and keeps only a few values live at a time.
+template <typename TA>
+__device__ __forceinline__ void mg_build_part1(const MgCtx<TA>& mg, const TA* kf0) {
+  const MgLevel<TA> L1 = mg.level(1);
+  for (int E = threadIdx.x; E < L1.NN; E += blockDim.x) mg_coarse_element<TA>(kf0, mg.n, E, L1.ke, L1.NN);
+  for (int l = 1; l < mg.levels; ++l) {
+    __syncthreads();
+    const MgLevel<TA> f = mg.level(l), c = mg.level(l + 1);
+    for (int E = threadIdx.x; E < c.NN; E += blockDim.x) mg_coarse_element<TA>(f.ke, f.n, E, c.ke, c.NN);
+  }
+}
+
+// Stencil block nb of node (i, j) summed from the element matrices ke ([36][n*n]) as it is
+// needed: one 2x2 block live at a time.
+template <typename TA>
+__device__ __forceinline__ void mg_stencil_block(const TA* ke, int n, int i, int j, int nb, TA (&blk)[4]) {
+  const int NN = n * n;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) blk[q] = TA(0);
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if ((offy(m) - offy(l) + 1) * 3 + (offx(m) - offx(l) + 1) != nb) continue;
+      const int slot = (i - offx(l) + n) % n + n * ((j - offy(l) + n) % n);
+#pragma unroll
+      for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) blk[2 * ii + kk] += ke[(size_t)tri8(2 * l + ii, 2 * m + kk) * NN + slot];
+    }
+}
+
+template <typename TA>
+__device__ __forceinline__ void mg_build_part2(const MgCtx<TA>& mg) {
+  const int tid = threadIdx.x;
+  __syncthreads();  // part 1's element matrices complete
+  for (int l = 1; l < mg.levels; ++l) {  // stencils and inverted blocks of the smoothing levels
+    const MgLevel<TA> v = mg.level(l);
+    for (int node = tid; node < v.NN; node += blockDim.x) {
+      const int i = node % v.n, j = node / v.n;
+#pragma unroll 1
+      for (int nb = 0; nb < 9; ++nb) {
+        TA blk[4];
+        mg_stencil_block<TA>(v.ke, v.n, i, j, nb, blk);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v.st[(size_t)(nb * 4 + q) * v.NN + node] = blk[q];
+        if (nb == 4) {
+          TA m[4];
+          invert_block<TA>(blk, node == 0, m);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v.mi[(size_t)q * v.NN + node] = m[q];
+        }
+      }
+    }
+  }
+  // coarsest: dense pinned matrix, one row per thread, then its inverse in place (warp 0)
+  const MgLevel<TA> c = mg.level(mg.levels);
+  const int D = 2 * c.NN, ld = D + 1;
+  TA* A = mg.coarsest_inverse();
+  if (tid < D) {
+    const int node = tid >> 1, ii = tid & 1, ni = node % c.n, nj = node / c.n;
+    for (int q = 0; q < D; ++q) A[(size_t)tid * ld + q] = TA(0);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {  // the four elements with this node as corner l
+      const int ei = (ni - offx(l) + c.n) % c.n, ej = (nj - offy(l) + c.n) % c.n, slot = ei + c.n * ej;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int nm = (ei + offx(m)) % c.n + c.n * ((ej + offy(m)) % c.n);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+          A[(size_t)tid * ld + 2 * nm + kk] += c.ke[(size_t)tri8(2 * l + ii, 2 * m + kk) * c.NN + slot];
+      }
+    }
+    if (tid < 2) {
+      for (int q = 0; q < D; ++q) A[(size_t)tid * ld + q] = q == tid ? TA(1) : TA(0);
+    } else {
+      A[(size_t)tid * ld] = TA(0);
+      A[(size_t)tid * ld + 1] = TA(0);
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {  // Gauss-Jordan inversion in place, lane = row (SPD: no pivoting)
+    for (int k = 0; k < D; ++k) {
+      const TA p = TA(1) / A[(size_t)k * ld + k];
+      __syncwarp();
+      if (tid == k) {
+        A[(size_t)k * ld + k] = TA(1);
+        for (int q = 0; q < D; ++q) A[(size_t)k * ld + q] *= p;
+      }
+      __syncwarp();
+      if (tid != k && tid < D) {
+        const TA f = A[(size_t)tid * ld + k];
+        A[(size_t)tid * ld + k] = TA(0);
+        for (int q = 0; q < D; ++q) A[(size_t)tid * ld + q] -= f * A[(size_t)k * ld + q];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// Coarse part of the V-cycle: the restricted residual is in level(1).r; on return
+// level(1).z holds the coarse correction.  All threads call it; ends with a barrier.
+template <typename TA>
+__device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
+  const int tid = threadIdx.x;
+  const TA om = (TA)kMgOmega;
+  for (int l = 1; l < mg.levels; ++l) {  // descend: pre-smooth, residual, restrict
+    const MgLevel<TA> v = mg.level(l), c = mg.level(l + 1);
+    if (tid < v.NN) v.z[tid] = mg_smooth<TA>(v.mi, v.NN, tid, v.r[tid], om);
+    __syncthreads();
+    if (tid < v.NN) {
+      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, tid), rr = v.r[tid];
+      v.t[tid] = mk2<TA>(rr.x - kz.x, rr.y - kz.y);
+    }
+    __syncthreads();
+    if (tid < c.NN) c.r[tid] = mg_restrict<TA>(v.t, v.n, tid);
+    __syncthreads();
+  }
+  {  // coarsest: z = A^-1 r (dof-wise; rows 0, 1 of the inverse are the pinned identity)
+    const MgLevel<TA> c = mg.level(mg.levels);
+    const int D = 2 * c.NN, ld = D + 1;
+    const TA* A = mg.coarsest_inverse();
+    const TA* r = reinterpret_cast<const TA*>(c.r);
+    if (tid < D) {
+      TA zz = TA(0);
+      for (int q = 0; q < D; ++q) zz += A[(size_t)tid * ld + q] * r[q];
+      reinterpret_cast<TA*>(c.z)[tid] = tid < 2 ? TA(0) : zz;
+    }
+    __syncthreads();
+  }
+  for (int l = mg.levels - 1; l >= 1; --l) {  // ascend: prolong, post-smooth
+    const MgLevel<TA> v = mg.level(l), c = mg.level(l + 1);
+    vec2_t<TA> z = mk2<TA>(TA(0), TA(0)), rr = z;
+    if (tid < v.NN) {
+      const vec2_t<TA> zo = v.z[tid], zp = mg_prolong<TA>(c.z, v.n, tid);
+      z = mk2<TA>(zo.x + zp.x, zo.y + zp.y);
+      v.z[tid] = z;
+      rr = v.r[tid];
+    }
+    __syncthreads();
+    if (tid < v.NN) {
+      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, tid);
+      const vec2_t<TA> dz = mg_smooth<TA>(v.mi, v.NN, tid, mk2<TA>(rr.x - kz.x, rr.y - kz.y), om);
+      z = mk2<TA>(z.x + dz.x, z.y + dz.y);
+    }
+    __syncthreads();
+    if (tid < v.NN) v.z[tid] = z;
+    __syncthreads();
+  }
+}
+
 // Block-Jacobi preconditioned CG for K x = b on the pinned periodic space, in the
 // single-reduction form of Chronopoulos and Gear (one fused block reduction of
 // gamma = r.u and delta = u.Ku per iteration, u = M^-1 r; p and s = K p follow by
@@ -443,24 +826,38 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* buf) {
 // negative curvature (p^T K p <= 0) the iteration stops with the step built so far
 // (Steihaug's truncated CG; on the first iteration the preconditioned residual direction with
 // |p^T K p| as curvature) and reports kStatusNegCurv, which the Newton loop accepts.
-template <typename TA, bool REG>
+template <typename TA, bool REG, bool kMG>
 __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& o, const TA (&Minv)[2][4],
-                                        const TA (&b)[4],
+                                        const MgCtx<TA>& mg, const TA (&b)[4],
                         vec2_t<TA>* xs, TA rtol, int max_it, vec2_t<TA>* ps, TA* red0, TA* red1, int* status,
                         bool truncate) {
+  // x: registers on the block-Jacobi path; accumulated in xs on the multigrid path, where the
+  // V-cycle needs the registers
   TA r[4], u[4], w[4], p[4], s[4], x[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     r[k] = o.active ? b[k] : TA(0);
     x[k] = TA(0);
+    u[k] = TA(0);
   }
-  auto precond = [&]() {  // u = M^-1 r with the inverted nodal 2x2 blocks (zero on idle threads)
+  auto x_axpy = [&](TA a, const TA (&v)[4]) {  // x += a v
+    if constexpr (kMG) {
+      if (o.active) {
+        const vec2_t<TA> x0 = xs[o.node[0]], x1 = xs[o.node[1]];
+        xs[o.node[0]] = mk2<TA>(x0.x + a * v[0], x0.y + a * v[1]);
+        xs[o.node[1]] = mk2<TA>(x1.x + a * v[2], x1.y + a * v[3]);
+      }
+    } else {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      u[2 * q] = Minv[q][0] * r[2 * q] + Minv[q][1] * r[2 * q + 1];
-      u[2 * q + 1] = Minv[q][2] * r[2 * q] + Minv[q][3] * r[2 * q + 1];
+      for (int k = 0; k < 4; ++k) x[k] += a * v[k];
     }
   };
+  if constexpr (kMG) {
+    if (o.active) {
+      xs[o.node[0]] = mk2<TA>(TA(0), TA(0));
+      xs[o.node[1]] = mk2<TA>(TA(0), TA(0));
+    }
+  }
   auto exchange_apply = [&]() {  // w = K u
     if (o.active) {
       ps[o.node[0]] = mk2<TA>(u[0], u[1]);
@@ -474,6 +871,49 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
       w[0] = w[1] = w[2] = w[3] = TA(0);
     }
   };
+  auto jacobi = [&](const TA (&v)[4], TA om) {  // u += om M^-1 v (inverted nodal 2x2 blocks)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      u[2 * q] += om * (Minv[q][0] * v[2 * q] + Minv[q][1] * v[2 * q + 1]);
+      u[2 * q + 1] += om * (Minv[q][2] * v[2 * q] + Minv[q][3] * v[2 * q + 1]);
+    }
+  };
+  auto precond = [&]() {  // u = M^-1 r: block-Jacobi, or the multigrid V-cycle
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = TA(0);
+    if (!kMG || !mg.levels) {
+      jacobi(r, TA(1));
+      return;
+    }
+    const TA om = (TA)kMgOmega;
+    jacobi(r, om);     // pre-smoothing from zero
+    exchange_apply();  // w = K u
+    __syncthreads();   // every read of ps done
+    if (o.active) {
+      ps[o.node[0]] = mk2<TA>(r[0] - w[0], r[1] - w[1]);
+      ps[o.node[1]] = mk2<TA>(r[2] - w[2], r[3] - w[3]);
+    }
+    __syncthreads();
+    {
+      const MgLevel<TA> c = mg.level(1);
+      for (int I = threadIdx.x; I < c.NN; I += blockDim.x) c.r[I] = mg_restrict<TA>(ps, o.n, I);
+    }
+    __syncthreads();
+    mg_coarse_cycle<TA>(mg);
+    if (o.active) {
+      const MgLevel<TA> c = mg.level(1);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const vec2_t<TA> zp = mg_prolong<TA>(c.z, o.n, o.node[q]);
+        u[2 * q] += zp.x;
+        u[2 * q + 1] += zp.y;
+      }
+    }
+    exchange_apply();  // w = K u (the restriction's reads of ps ended before the coarse barriers)
+    const TA t[4] = {r[0] - w[0], r[1] - w[1], r[2] - w[2], r[3] - w[3]};
+    jacobi(t, om);     // post-smoothing
+    __syncthreads();   // every read of ps done before the caller's exchange
+  };
   *status = kStatusOk;
   precond();
   exchange_apply();
@@ -486,8 +926,7 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
     if (!(delta > TA(0))) {
       if (truncate && delta < TA(0)) {
         const TA a0 = cg_div<TA>(gamma, -delta);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) x[k] = a0 * u[k];
+        x_axpy(a0, u);
         *status = kStatusNegCurv;
       } else {
         *status = kStatusPcgBreakdown;
@@ -505,11 +944,9 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
           *status = kStatusPcgCap;
           break;
         }
+        x_axpy(alpha, p);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          x[k] += alpha * p[k];
-          r[k] -= alpha * s[k];
-        }
+        for (int k = 0; k < 4; ++k) r[k] -= alpha * s[k];
         precond();
         exchange_apply();
         TA gn = r[0] * u[0] + r[1] * u[1] + r[2] * u[2] + r[3] * u[3];
@@ -533,31 +970,22 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
       }
     }
   }
-  if (o.active) {
+  if (!kMG && o.active) {
     xs[o.node[0]] = mk2<TA>(x[0], x[1]);
     xs[o.node[1]] = mk2<TA>(x[2], x[3]);
   }
   return it;
 }
 
-template <typename TA>
-__device__ __forceinline__ void invert_block(const TA (&Kself)[4], bool pinned, TA (&Mi)[4]) {
-  const TA det = Kself[0] * Kself[3] - Kself[1] * Kself[2];
-  const TA id = pinned ? TA(0) : TA(1) / det;
-  Mi[0] = Kself[3] * id;
-  Mi[1] = -Kself[1] * id;
-  Mi[2] = -Kself[2] * id;
-  Mi[3] = Kself[0] * id;
-}
 
 // Assemble the tangent at the current w: element tangents -> stage, stencil gather, Minv.
 // Minv (inverted nodal blocks, zero on idle threads and the pinned node) stays in
 // registers; with withL the condensation right-hand sides go to shared memory,
 // Lb[c][NN] = -L_c of each owned node.
-template <typename TA, bool REG>
+template <typename TA, bool REG, bool kMG>
 __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& sm, TA* stage_k,
                                               const TA (&Fb)[4], const uint8_t* phase, Stencil<TA, REG>& S,
-                                              TA (&Minv)[2][4], bool withL, vec2_t<TA>* Lb) {
+                                              TA (&Minv)[2][4], bool withL, vec2_t<TA>* Lb, const MgCtx<TA>& mg) {
   TA L[2][2][4];
   const int n = o.n, NN = o.NN;
   const vec2_t<TA>* wsrc;
@@ -575,6 +1003,7 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
     }
   }
   __syncthreads();
+  if (kMG && mg.levels) mg_build_part1<TA>(mg, stage_k);  // reads the staged element tangents
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     TA Kn[9][4];
@@ -630,6 +1059,7 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
       }
     }
   }
+  if (kMG && mg.levels) mg_build_part2<TA>(mg);  // ends with a barrier
 }
 
 // Energy form of the tangent transfer over this thread's two elements (FP64 sums of
@@ -697,7 +1127,7 @@ __device__ __forceinline__ void element_transfer(int e, int n, const vec2_t<TA>*
 
 // kFixed: one grid size for the whole batch, arrays indexed arithmetically (qp -> RVE qp or 0,
 // fluctuation of qp at qp*2*n*n) instead of through the context's index tables.
-template <typename TA, bool kFixed = false>
+template <typename TA, bool kFixed, bool kMG>
 __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, TA* gscr) {
   constexpr bool REG = std::is_same<TA, float>::value;
   const int tid = threadIdx.x;
@@ -725,6 +1155,19 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   Stencil<TA, REG> S;
   S.g = gscr;
   S.NN = NN;
+  // multigrid levels: fast region after the condensation arrays in the stage area (mixed) or
+  // after the staged tangents and stencil in the block scratch (FP64); slow region in the
+  // block scratch
+  MgCtx<TA> mg;
+  mg.n = n;
+  mg.levels = (kMG && a.mg) ? mg_levels(n) : 0;
+  if constexpr (REG) {
+    mg.fast = reinterpret_cast<TA*>(sm.stage + 8 * (size_t)NN * sizeof(vec2_t<TA>));
+    mg.slow = reinterpret_cast<TA*>(a.scratch) + (size_t)blockIdx.x * a.scratch_stride;
+  } else {
+    mg.fast = gscr + (size_t)72 * a.nn_max;
+    mg.slow = mg.fast + mg_fast_max(a.nn_max);
+  }
   TA* redA = reinterpret_cast<TA*>(sm.red);
   TA* redB = reinterpret_cast<TA*>(sm.red + 512);
   vec2_t<TA>* Xs = reinterpret_cast<vec2_t<TA>*>(sm.stage);  // [4][NN]
@@ -817,13 +1260,14 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       // ---- tangent and PCG correction
       {
         const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
-        build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb);
+        build_tangent<TA, REG, kMG>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb, mg);
       }
       TA b[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) b[k] = (TA)(-R[k]);
       int pst = kStatusOk;
-      cg_total += pcg_pair<TA, REG>(S, o, Minv, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redA, redB, &pst, true);
+      cg_total += pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redA, redB,
+                                         &pst, true);
       if (pst == kStatusPcgBreakdown) {
         status = kStatusPcgBreakdown;
         break;
@@ -897,7 +1341,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   const bool want_A = usable && !(a.flags & kFlagNoTangent) && a.A != nullptr;
   if (want_A) {
     const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
-    build_tangent<TA, REG>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb);
+    build_tangent<TA, REG, kMG>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb, mg);
     vec2_t<TA>* X = Xs;
     for (int c = 0; c < 4; ++c) {
       TA b[4] = {TA(0), TA(0), TA(0), TA(0)};
@@ -909,7 +1353,8 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
         b[3] = b1.y;
       }
       int pst = kStatusOk;
-      const int ci = pcg_pair<TA, REG>(S, o, Minv, b, X + c * NN, (TA)a.cond_rtol, a.max_cond_cg, sm.p, redA, redB,
+      const int ci = pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, X + c * NN, (TA)a.cond_rtol, a.max_cond_cg, sm.p,
+                                            redA, redB,
                                         &pst, false);
       cond_total += ci;
       cond_max = ci > cond_max ? ci : cond_max;
@@ -968,21 +1413,21 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   __syncthreads();
 }
 
-template <typename TA, bool kFixed = false>
+template <typename TA, bool kFixed, bool kMG>
 __global__ void __launch_bounds__(kThreads2D, 1) rve2d_kernel(const Rve2dArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem2D<TA> sm;
   smem2d_layout<TA>(a.nn_max, &sm, smem_raw);
   __shared__ int s_item;
   constexpr bool REG = std::is_same<TA, float>::value;
-  TA* gscr = REG ? nullptr : reinterpret_cast<TA*>(a.scratch) + (size_t)blockIdx.x * 72 * a.nn_max;
+  TA* gscr = REG ? nullptr : reinterpret_cast<TA*>(a.scratch) + (size_t)blockIdx.x * a.scratch_stride;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
     __syncthreads();
     const int item = s_item;
     __syncthreads();
     if (item >= (a.n_dev ? *a.n_dev : a.n_qp)) break;
-    solve_item_2d<TA, kFixed>(a, kFixed ? item : a.order[item], sm, gscr);
+    solve_item_2d<TA, kFixed, kMG>(a, kFixed ? item : a.order[item], sm, gscr);
   }
 }
 
@@ -992,35 +1437,42 @@ size_t rve2d_smem_bytes(int nn_max, bool mixed) {
   return mixed ? smem2d_layout<float>(nn_max, nullptr, nullptr) : smem2d_layout<double>(nn_max, nullptr, nullptr);
 }
 
+long long rve2d_scratch_stride(int nn_max, bool mixed) {
+  return mixed ? mg_slow_max(nn_max) : 72LL * nn_max + mg_fast_max(nn_max) + mg_slow_max(nn_max);
+}
+
 size_t rve2d_scratch_bytes(int nn_max, bool mixed, int n_blocks) {
-  return mixed ? 0 : sizeof(double) * 72 * (size_t)nn_max * n_blocks;
+  return (mixed ? sizeof(float) : sizeof(double)) * (size_t)rve2d_scratch_stride(nn_max, mixed) * n_blocks;
 }
 
 int rve2d_threads() { return kThreads2D; }
 
-cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream) {
-  const size_t smem = rve2d_smem_bytes(a.nn_max, mixed);
-  cudaError_t err;
-  if (mixed) {
-    err = cudaFuncSetAttribute(rve2d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    rve2d_kernel<float><<<n_blocks, kThreads2D, smem, stream>>>(a);
-  } else {
-    err = cudaFuncSetAttribute(rve2d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    rve2d_kernel<double><<<n_blocks, kThreads2D, smem, stream>>>(a);
-  }
+template <typename TA, bool kMG>
+cudaError_t launch_variant(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream) {
+  const cudaError_t err =
+      cudaFuncSetAttribute(rve2d_kernel<TA, false, kMG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  rve2d_kernel<TA, false, kMG><<<n_blocks, kThreads2D, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
-// FP64 kernel over a fixed-layout batch with caller-provided scratch (the no-allocation
-// entry point in noalloc.cu supplies its static device array).
+// The multigrid and block-Jacobi paths are separate instantiations, so each is register-
+// allocated on its own.
+cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream) {
+  const size_t smem = rve2d_smem_bytes(a.nn_max, mixed);
+  if (mixed)
+    return a.mg ? launch_variant<float, true>(a, n_blocks, smem, stream)
+                : launch_variant<float, false>(a, n_blocks, smem, stream);
+  return a.mg ? launch_variant<double, true>(a, n_blocks, smem, stream)
+              : launch_variant<double, false>(a, n_blocks, smem, stream);
+}
+
 cudaError_t rve2d_launch_fixed_fp64(const Rve2dArgs& a, int n_blocks, cudaStream_t stream) {
   const size_t smem = rve2d_smem_bytes(a.nn_max, false);
-  cudaError_t err = cudaFuncSetAttribute(rve2d_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t err = cudaFuncSetAttribute(rve2d_kernel<double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
-  rve2d_kernel<double, true><<<n_blocks, kThreads2D, smem, stream>>>(a);
+  rve2d_kernel<double, true, false><<<n_blocks, kThreads2D, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

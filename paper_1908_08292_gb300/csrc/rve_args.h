@@ -29,6 +29,8 @@ struct Rve2dArgs {
   double newton_rtol, newton_atol, cg_rtol, cond_rtol;
   int max_newton, max_cg, max_cond_cg, flags;
   int retry_stages;      // > 1: load continuation from w = 0 after a failed Newton solve
+  int mg;                // 1: multigrid-preconditioned PCG where the grid allows it (2D)
+  long long scratch_stride;  // per-block scratch, in elements of the kernel's arithmetic type (2D)
   const int32_t* n_dev;  // optional: number of work items in device memory (order = a qp list)
   int fixed_n;        // fixed-layout launches only: grid size of every RVE
   int phase_per_qp;   // fixed-layout launches only: 1 = one phase map per qp, 0 = one shared
@@ -36,6 +38,7 @@ struct Rve2dArgs {
 
 size_t rve2d_smem_bytes(int nn_max, bool mixed);
 size_t rve2d_scratch_bytes(int nn_max, bool mixed, int n_blocks);
+long long rve2d_scratch_stride(int nn_max, bool mixed);
 int rve2d_threads();
 cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream);
 cudaError_t rve2d_launch_fixed_fp64(const Rve2dArgs& a, int n_blocks, cudaStream_t stream);
