@@ -76,7 +76,9 @@ __host__ __device__ inline long long mg_fast_elems(int n) {
     e += 36 * nn + 4 * nn + 3 * 2 * nn;  // stencil, Minv, r/z/t
   }
   const long long nc = (long long)(n >> L) * (n >> L), D = 2 * nc;
-  return e + 2 * 2 * nc + D * (D + 1);  // r/z, inverse (row stride D + 1)
+  // fine-level residual, coarsest r/z and its inverse (row stride D + 1; two buffers for the
+  // out-of-place Gauss-Jordan steps)
+  return 2LL * n * n + e + 2 * 2 * nc + 2 * D * (D + 1);
 }
 __host__ __device__ inline long long mg_slow_elems(int n) {
   const int L = mg_levels(n);
@@ -528,10 +530,12 @@ struct MgCtx {
   int n;       // fine grid
   TA* fast;
   TA* slow;
+  // fine-level residual (restriction input), at the start of the fast region
+  __device__ __forceinline__ vec2_t<TA>* fine_t() const { return reinterpret_cast<vec2_t<TA>*>(fast); }
   // view of coarse level l (1..levels); the coarsest has no st/mi/t, its inverse follows r, z
   __device__ __forceinline__ MgLevel<TA> level(int l) const {
     MgLevel<TA> v;
-    TA* f = fast;
+    TA* f = fast + 2 * n * n;
     TA* k = slow;
     for (int q = 1; q < l; ++q) {
       const int nn = (n >> q) * (n >> q);
@@ -604,15 +608,20 @@ __device__ __forceinline__ void mg_coarse_element(const TA* kf, int nf, int E, T
   for (int q = 0; q < 36; ++q) kc[(size_t)q * nnc + E] = acc[q];
 }
 
-// y = K_l z at node v of a coarse level (zero at the pinned node).
+// Periodic neighbours without integer division.
+__device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int wrap_inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
+
+// y = K_l z at node v = (i, j) of a coarse level (zero at the pinned node).
 template <typename TA>
-__device__ __forceinline__ vec2_t<TA> mg_apply(const MgLevel<TA>& L, const vec2_t<TA>* z, int v) {
-  const int n = L.n, i = v % n, j = v / n;
+__device__ __forceinline__ vec2_t<TA> mg_apply(const MgLevel<TA>& L, const vec2_t<TA>* z, int i, int j) {
+  const int n = L.n, v = i + n * j;
+  const int cols[3] = {wrap_dec(i, n), i, wrap_inc(i, n)};
+  const int rows[3] = {wrap_dec(j, n) * n, j * n, wrap_inc(j, n) * n};
   TA yx = TA(0), yy = TA(0);
 #pragma unroll
   for (int nb = 0; nb < 9; ++nb) {
-    const int dx = nb % 3 - 1, dy = nb / 3 - 1;
-    const vec2_t<TA> zn = z[(i + dx + n) % n + n * ((j + dy + n) % n)];
+    const vec2_t<TA> zn = z[rows[nb / 3] + cols[nb % 3]];
     yx += L.st[(size_t)(nb * 4 + 0) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 1) * L.NN + v] * zn.y;
     yy += L.st[(size_t)(nb * 4 + 2) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 3) * L.NN + v] * zn.y;
   }
@@ -626,28 +635,30 @@ __device__ __forceinline__ vec2_t<TA> mg_smooth(const TA* mi, int NN, int v, vec
 }
 
 // Full-weighting restriction (the transpose of bilinear prolongation) of the fine vector t
-// (grid nf) to coarse node I; zero at the pinned node.
+// (grid nf) to coarse node (I, J); zero at the pinned node.
 template <typename TA>
-__device__ __forceinline__ vec2_t<TA> mg_restrict(const vec2_t<TA>* t, int nf, int I) {
-  const int nc = nf >> 1, ix = 2 * (I % nc), jy = 2 * (I / nc);
+__device__ __forceinline__ vec2_t<TA> mg_restrict(const vec2_t<TA>* t, int nf, int I, int J) {
+  const int ix = 2 * I, jy = 2 * J;
+  const int cols[3] = {wrap_dec(ix, nf), ix, ix + 1};
+  const int rows[3] = {wrap_dec(jy, nf) * nf, jy * nf, (jy + 1) * nf};
   TA sx = TA(0), sy = TA(0);
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy)
+  for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const TA wgt = TA((dx == 0 ? 1.0f : 0.5f) * (dy == 0 ? 1.0f : 0.5f));
-      const vec2_t<TA> v = t[(ix + dx + nf) % nf + nf * ((jy + dy + nf) % nf)];
+    for (int dx = 0; dx < 3; ++dx) {
+      const TA wgt = TA((dx == 1 ? 1.0f : 0.5f) * (dy == 1 ? 1.0f : 0.5f));
+      const vec2_t<TA> v = t[rows[dy] + cols[dx]];
       sx += wgt * v.x;
       sy += wgt * v.y;
     }
-  return I == 0 ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(sx, sy);
+  return (I == 0 && J == 0) ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(sx, sy);
 }
 
-// Bilinear prolongation of the coarse vector zc (grid nf/2) to fine node v of grid nf.
+// Bilinear prolongation of the coarse vector zc (grid nf/2) to fine node (i, j) of grid nf.
 template <typename TA>
-__device__ __forceinline__ vec2_t<TA> mg_prolong(const vec2_t<TA>* zc, int nf, int v) {
-  const int nc = nf >> 1, i = v % nf, j = v / nf;
-  const int i0 = i >> 1, j0 = j >> 1, i1 = (i0 + 1) % nc, j1 = (j0 + 1) % nc;
+__device__ __forceinline__ vec2_t<TA> mg_prolong(const vec2_t<TA>* zc, int nf, int i, int j) {
+  const int nc = nf >> 1;
+  const int i0 = i >> 1, j0 = j >> 1, i1 = wrap_inc(i0, nc), j1 = wrap_inc(j0, nc);
   const vec2_t<TA> a = zc[i0 + nc * j0];
   if (!(i & 1) && !(j & 1)) return a;
   if (!(i & 1)) {  // between two coarse rows
@@ -719,10 +730,12 @@ __device__ __forceinline__ void mg_build_part2(const MgCtx<TA>& mg) {
       }
     }
   }
-  // coarsest: dense pinned matrix, one row per thread, then its inverse in place (warp 0)
+  // coarsest: dense pinned matrix (one row per thread), then its inverse by Gauss-Jordan
+  // elimination, one pivot per step over the whole block, alternating between two buffers
   const MgLevel<TA> c = mg.level(mg.levels);
   const int D = 2 * c.NN, ld = D + 1;
   TA* A = mg.coarsest_inverse();
+  TA* B = A + (size_t)D * ld;
   if (tid < D) {
     const int node = tid >> 1, ii = tid & 1, ni = node % c.n, nj = node / c.n;
     for (int q = 0; q < D; ++q) A[(size_t)tid * ld + q] = TA(0);
@@ -745,73 +758,91 @@ __device__ __forceinline__ void mg_build_part2(const MgCtx<TA>& mg) {
     }
   }
   __syncthreads();
-  if (tid < 32) {  // Gauss-Jordan inversion in place, lane = row (SPD: no pivoting)
-    for (int k = 0; k < D; ++k) {
-      const TA p = TA(1) / A[(size_t)k * ld + k];
-      __syncwarp();
-      if (tid == k) {
-        A[(size_t)k * ld + k] = TA(1);
-        for (int q = 0; q < D; ++q) A[(size_t)k * ld + q] *= p;
-      }
-      __syncwarp();
-      if (tid != k && tid < D) {
-        const TA f = A[(size_t)tid * ld + k];
-        A[(size_t)tid * ld + k] = TA(0);
-        for (int q = 0; q < D; ++q) A[(size_t)tid * ld + q] -= f * A[(size_t)k * ld + q];
-      }
-      __syncwarp();
-    }
+  // entries (i, j) of this thread: e and e + blockDim.x (D*D <= 1024 = 2 x 512)
+  const int e0 = tid, e1 = tid + blockDim.x;
+  const int i0 = e0 / D, j0 = e0 % D, i1 = e1 / D, j1 = e1 % D;
+  for (int k = 0; k < D; ++k) {  // SPD: no pivoting; D is even, so the result ends in A
+    const TA* Ao = (k & 1) ? B : A;
+    TA* An = (k & 1) ? A : B;
+    const TA ip = TA(1) / Ao[(size_t)k * ld + k];
+    auto step = [&](int i, int j) {
+      const TA aik = Ao[(size_t)i * ld + k], akj = Ao[(size_t)k * ld + j];
+      TA v;
+      if (i == k) v = (j == k) ? ip : akj * ip;
+      else v = (j == k) ? -aik * ip : Ao[(size_t)i * ld + j] - aik * akj * ip;
+      An[(size_t)i * ld + j] = v;
+    };
+    if (e0 < D * D) step(i0, j0);
+    if (e1 < D * D) step(i1, j1);
+    __syncthreads();
   }
-  __syncthreads();
 }
 
-// Coarse part of the V-cycle: the restricted residual is in level(1).r; on return
-// level(1).z holds the coarse correction.  All threads call it; ends with a barrier.
+// Restricted residual of coarse node t of level l (from the residual t_f of the finer grid nf),
+// stored with its pre-smoothed correction when level l is a smoothing level: the smoothing is
+// local to the node, so it needs no barrier of its own.
+template <typename TA>
+__device__ __forceinline__ void mg_restrict_smooth(const MgCtx<TA>& mg, int l, const vec2_t<TA>* tf, int nf, int t) {
+  const MgLevel<TA> c = mg.level(l);
+  const vec2_t<TA> r = mg_restrict<TA>(tf, nf, t % c.n, t / c.n);
+  c.r[t] = r;
+  if (l < mg.levels) c.z[t] = mg_smooth<TA>(c.mi, c.NN, t, r, (TA)kMgOmega);
+}
+
+// Where the corrected z of level l ends: the t vector of a smoothing level (free on the way
+// up), the z vector of the coarsest.
+template <typename TA>
+__device__ __forceinline__ const vec2_t<TA>* mg_result(const MgCtx<TA>& mg, int l) {
+  const MgLevel<TA> v = mg.level(l);
+  return l == mg.levels ? v.z : v.t;
+}
+
+// Coarse part of the V-cycle.  On entry level(1) holds the restricted residual (and, for a
+// smoothing level, its pre-smoothed z); on return mg_result(mg, 1) holds the coarse
+// correction.  Two block barriers per level each way.  All threads call it; ends with a barrier.
+// (Running the small levels in one warp with warp barriers was measured slower: the other warps
+// idle while one warp walks the level's nodes serially.)
 template <typename TA>
 __device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
   const int tid = threadIdx.x;
   const TA om = (TA)kMgOmega;
-  for (int l = 1; l < mg.levels; ++l) {  // descend: pre-smooth, residual, restrict
-    const MgLevel<TA> v = mg.level(l), c = mg.level(l + 1);
-    if (tid < v.NN) v.z[tid] = mg_smooth<TA>(v.mi, v.NN, tid, v.r[tid], om);
-    __syncthreads();
+  for (int l = 1; l < mg.levels; ++l) {  // descend: residual, restrict (+ next pre-smoothing)
+    const MgLevel<TA> v = mg.level(l);
     if (tid < v.NN) {
-      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, tid), rr = v.r[tid];
+      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, tid % v.n, tid / v.n), rr = v.r[tid];
       v.t[tid] = mk2<TA>(rr.x - kz.x, rr.y - kz.y);
     }
     __syncthreads();
-    if (tid < c.NN) c.r[tid] = mg_restrict<TA>(v.t, v.n, tid);
+    if (tid < mg.level(l + 1).NN) mg_restrict_smooth<TA>(mg, l + 1, v.t, v.n, tid);
     __syncthreads();
   }
-  {  // coarsest: z = A^-1 r (dof-wise; rows 0, 1 of the inverse are the pinned identity)
+  {  // coarsest: z = A^-1 r, 16 lanes per row (rows 0, 1 of the inverse: the pinned identity)
     const MgLevel<TA> c = mg.level(mg.levels);
-    const int D = 2 * c.NN, ld = D + 1;
+    const int D = 2 * c.NN, ld = D + 1, row = tid >> 4, l16 = tid & 15;
     const TA* A = mg.coarsest_inverse();
     const TA* r = reinterpret_cast<const TA*>(c.r);
-    if (tid < D) {
-      TA zz = TA(0);
-      for (int q = 0; q < D; ++q) zz += A[(size_t)tid * ld + q] * r[q];
-      reinterpret_cast<TA*>(c.z)[tid] = tid < 2 ? TA(0) : zz;
-    }
+    TA zz = TA(0);
+    if (row < D)
+      for (int q = l16; q < D; q += 16) zz += A[(size_t)row * ld + q] * r[q];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
+    if (row < D && l16 == 0) reinterpret_cast<TA*>(c.z)[row] = row < 2 ? TA(0) : zz;
     __syncthreads();
   }
-  for (int l = mg.levels - 1; l >= 1; --l) {  // ascend: prolong, post-smooth
-    const MgLevel<TA> v = mg.level(l), c = mg.level(l + 1);
-    vec2_t<TA> z = mk2<TA>(TA(0), TA(0)), rr = z;
+  for (int l = mg.levels - 1; l >= 1; --l) {  // ascend: prolong, post-smooth into t
+    const MgLevel<TA> v = mg.level(l);
+    const vec2_t<TA>* zc = mg_result<TA>(mg, l + 1);
+    const int i = tid % v.n, j = tid / v.n;
     if (tid < v.NN) {
-      const vec2_t<TA> zo = v.z[tid], zp = mg_prolong<TA>(c.z, v.n, tid);
-      z = mk2<TA>(zo.x + zp.x, zo.y + zp.y);
-      v.z[tid] = z;
-      rr = v.r[tid];
+      const vec2_t<TA> zo = v.z[tid], zp = mg_prolong<TA>(zc, v.n, i, j);
+      v.z[tid] = mk2<TA>(zo.x + zp.x, zo.y + zp.y);
     }
     __syncthreads();
     if (tid < v.NN) {
-      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, tid);
+      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, i, j), rr = v.r[tid], z = v.z[tid];
       const vec2_t<TA> dz = mg_smooth<TA>(v.mi, v.NN, tid, mk2<TA>(rr.x - kz.x, rr.y - kz.y), om);
-      z = mk2<TA>(z.x + dz.x, z.y + dz.y);
+      v.t[tid] = mk2<TA>(z.x + dz.x, z.y + dz.y);
     }
-    __syncthreads();
-    if (tid < v.NN) v.z[tid] = z;
     __syncthreads();
   }
 }
@@ -888,28 +919,28 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
     const TA om = (TA)kMgOmega;
     jacobi(r, om);     // pre-smoothing from zero
     exchange_apply();  // w = K u
-    __syncthreads();   // every read of ps done
+    vec2_t<TA>* ft = mg.fine_t();
     if (o.active) {
-      ps[o.node[0]] = mk2<TA>(r[0] - w[0], r[1] - w[1]);
-      ps[o.node[1]] = mk2<TA>(r[2] - w[2], r[3] - w[3]);
+      ft[o.node[0]] = mk2<TA>(r[0] - w[0], r[1] - w[1]);
+      ft[o.node[1]] = mk2<TA>(r[2] - w[2], r[3] - w[3]);
     }
     __syncthreads();
     {
       const MgLevel<TA> c = mg.level(1);
-      for (int I = threadIdx.x; I < c.NN; I += blockDim.x) c.r[I] = mg_restrict<TA>(ps, o.n, I);
+      for (int I = threadIdx.x; I < c.NN; I += blockDim.x) mg_restrict_smooth<TA>(mg, 1, ft, o.n, I);
     }
     __syncthreads();
     mg_coarse_cycle<TA>(mg);
     if (o.active) {
-      const MgLevel<TA> c = mg.level(1);
+      const vec2_t<TA>* zc = mg_result<TA>(mg, 1);
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const vec2_t<TA> zp = mg_prolong<TA>(c.z, o.n, o.node[q]);
+        const vec2_t<TA> zp = mg_prolong<TA>(zc, o.n, o.col, 2 * o.strip + q);
         u[2 * q] += zp.x;
         u[2 * q + 1] += zp.y;
       }
     }
-    exchange_apply();  // w = K u (the restriction's reads of ps ended before the coarse barriers)
+    exchange_apply();  // w = K u (every read of ps by the first apply ended before the barriers)
     const TA t[4] = {r[0] - w[0], r[1] - w[1], r[2] - w[2], r[3] - w[3]};
     jacobi(t, om);     // post-smoothing
     __syncthreads();   // every read of ps done before the caller's exchange
