@@ -198,12 +198,50 @@ struct Scratch3 {
   TA* s;        // [3][NN]
   TA* mi;       // [6][NN] inverted diagonal blocks (xx, xy, xz, yy, yz, zz)
   TA* L;        // [9][3][NN] transfer right-hand sides
+  TA* mg;       // multigrid levels (mg3_elems)
 };
+
+// ------------------------------------------------------------ multigrid sizes (3D)
+// Coarse levels: halve while the grid is even and above 3 (16 -> 8, 4, 2; 12 -> 6, 3; 8 -> 4, 2);
+// 0 when the hierarchy does not end at 2 or 3 nodes per axis.
+__host__ __device__ inline int mg3_levels(int n) {
+  int l = 0, m = n;
+  while (m > 3 && (m & 1) == 0) {
+    m >>= 1;
+    ++l;
+  }
+  return (m <= 3 && l >= 1) ? l : 0;
+}
+// Elements (TA) of the multigrid region for grid n: per coarse level the element blocks
+// [36][9][NE], the inverted nodal blocks [6][NN] and r, z, t [3][NN]; then the coarsest
+// inverse (two buffers of D x (D + 1), D = 3 NN_c).
+__host__ __device__ inline long long mg3_elems(int n) {
+  const int L = mg3_levels(n);
+  if (!L) return 0;
+  long long e = 0;
+  for (int l = 1; l <= L; ++l) {
+    const long long m = n >> l, nn = m * m * m;
+    e += 324 * nn + 6 * nn + 9 * nn;
+  }
+  const long long m = n >> L, D = 3 * m * m * m;
+  return e + 2 * D * (D + 1);
+}
+__host__ __device__ inline long long mg3_elems_max(int nn_max) {
+  long long mx = 0;
+  for (int n = 2; n * n * n <= nn_max; ++n) mx = mg3_elems(n) > mx ? mg3_elems(n) : mx;
+  return mx;
+}
+
+template <typename TA>
+__host__ __device__ inline size_t scratch3_base_bytes(int NN) {
+  const size_t b = sizeof(double) * 24 * (size_t)NN +
+                   sizeof(TA) * ((size_t)kQp3 * 8 * NN + 4 * 3 * (size_t)NN + 6 * (size_t)NN + 27 * (size_t)NN);
+  return (b + 255) & ~size_t(255);
+}
 
 template <typename TA>
 __host__ __device__ inline size_t scratch3_bytes(int NN) {
-  const size_t b = sizeof(double) * 24 * (size_t)NN +
-                   sizeof(TA) * ((size_t)kQp3 * 8 * NN + 4 * 3 * (size_t)NN + 6 * (size_t)NN + 27 * (size_t)NN);
+  const size_t b = scratch3_base_bytes<TA>(NN) + sizeof(TA) * (size_t)mg3_elems_max(NN);
   return (b + 255) & ~size_t(255);  // every block's scratch starts 256-byte aligned
 }
 
@@ -225,6 +263,7 @@ __device__ inline Scratch3<TA> scratch3_layout(unsigned char* base, int NN) {
   s.mi = t;
   t += 6 * (size_t)NN;
   s.L = t;
+  s.mg = reinterpret_cast<TA*>(base + scratch3_base_bytes<TA>(NN));
   return s;
 }
 
@@ -248,9 +287,47 @@ __device__ __forceinline__ void block_sum_n(T* v, int nv, T* buf) {
 }
 
 template <typename TA>
+struct Mg3Level {
+  int n, NN;
+  TA* kb;  // [36 block pairs a <= b][9][NN] element blocks (row-major 3x3)
+  TA* mi;  // [6][NN] inverted nodal diagonal blocks (zero at node 0)
+  TA* r;   // [3][NN]
+  TA* z;   // [3][NN]
+  TA* t;   // [3][NN]
+};
+
+template <typename TA>
+struct Mg3 {
+  int levels = 0;  // coarse levels, 0 = block-Jacobi
+  int n = 0;       // fine grid
+  TA* base = nullptr;
+  __device__ __forceinline__ Mg3Level<TA> level(int l) const {
+    TA* p = base;
+    for (int q = 1; q < l; ++q) {
+      const int m = n >> q;
+      p += 339 * m * m * m;
+    }
+    Mg3Level<TA> v;
+    v.n = n >> l;
+    v.NN = v.n * v.n * v.n;
+    v.kb = p;
+    v.mi = p + 324 * v.NN;
+    v.r = v.mi + 6 * v.NN;
+    v.z = v.r + 3 * v.NN;
+    v.t = v.z + 3 * v.NN;
+    return v;
+  }
+  __device__ __forceinline__ TA* inverse() const {
+    const Mg3Level<TA> c = level(levels);
+    return c.t + 3 * c.NN;
+  }
+};
+
+template <typename TA>
 struct Ctx3 {
   Geo3 g;
   int NE;
+  Mg3<TA> mg;
   const uint8_t* phase;
   const double* lame;  // shared [kMaxPhase][2]
   Scratch3<TA> sc;
@@ -496,6 +573,375 @@ __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ multigrid (3D)
+// Geometric V(1,1)-cycle used as the PCG preconditioner (same construction as in 2D): Galerkin
+// coarse operators stored as element blocks, coarse node 0 without a basis function (every
+// level pinned at node 0), damped 3x3 block-Jacobi smoothing (omega = 0.7), coarsest level
+// (2^3 or 3^3 nodes) solved through its dense inverse.  The first coarse level is integrated
+// directly from the fine Gauss-point data (Fit, hb, gm): its element blocks are
+//   K_E(a,b)_ik = sum over the 64 fine Gauss points of E of
+//                 w [mu d_ik g_a.g_b + gm v_a,i v_b,k - hb v_b,i v_a,k],  v = Fit g,
+// with g the gradients of E's trilinear shape functions — the fine bilinear form evaluated on
+// the coarse functions, i.e. P^T K P.  Deeper levels follow from the element blocks with the
+// trilinear weights.  All multigrid data live in the block's global scratch; coarse applies
+// gather per node (no atomics).
+constexpr float kMg3Omega = 0.7f;
+
+__host__ __device__ constexpr int pair8(int a, int b) {  // a <= b
+  return a * 8 - (a * (a - 1)) / 2 + (b - a);
+}
+
+// block (a, b) entry (i, k) of element E (any order of a, b: symmetric storage)
+template <typename TA>
+__device__ __forceinline__ TA mg3_kb(const Mg3Level<TA>& L, int E, int a, int b, int i, int k) {
+  return a <= b ? L.kb[(size_t)(pair8(a, b) * 9 + 3 * i + k) * L.NN + E]
+                : L.kb[(size_t)(pair8(b, a) * 9 + 3 * k + i) * L.NN + E];
+}
+
+__device__ __forceinline__ int node3(int n, int i, int j, int k) { return i + n * (j + n * k); }
+
+// level 1 element blocks, task (E, a): row block a, b >= a, from the fine Gauss-point data
+template <typename TA>
+__device__ __noinline__ void mg3_build_level1(const Ctx3<TA>& c) {
+  const Mg3Level<TA> L = c.mg.level(1);
+  const int n = c.g.n, nc = L.n;
+  const TA ihc = (TA)nc, wq = TA(0.125) / ((TA)n * (TA)n * (TA)n);
+  for (int task = threadIdx.x; task < 8 * L.NN; task += blockDim.x) {
+    const int E = task >> 3, a = task & 7;
+    const int I = E % nc, J = (E / nc) % nc, K = E / (nc * nc);
+    const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+    TA acc[8][9];
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int q = 0; q < 9; ++q) acc[b][q] = TA(0);
+    for (int sub = 0; sub < 8; ++sub) {
+      const int sx = sub & 1, sy = (sub >> 1) & 1, sz = sub >> 2;
+      const int e = node3(n, 2 * I + sx, 2 * J + sy, 2 * K + sz);
+      const TA mu = (TA)c.lame[2 * c.phase[e] + 1];
+#pragma unroll 1
+      for (int q = 0; q < 8; ++q) {
+        const TA xi = TA(0.5) * ((TA)sx + (TA)g01(q & 1)), et = TA(0.5) * ((TA)sy + (TA)g01((q >> 1) & 1)),
+                 ze = TA(0.5) * ((TA)sz + (TA)g01(q >> 2));
+        TA qv[12];
+        load_qp(c.sc.qpd, c.NE, q, e, qv);
+        const TA gax = ihc * (ax ? TA(1) : TA(-1)) * phi(ay, et) * phi(az, ze);
+        const TA gay = ihc * (ay ? TA(1) : TA(-1)) * phi(ax, xi) * phi(az, ze);
+        const TA gaz = ihc * (az ? TA(1) : TA(-1)) * phi(ax, xi) * phi(ay, et);
+        TA va[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) va[i] = qv[3 * i] * gax + qv[3 * i + 1] * gay + qv[3 * i + 2] * gaz;
+        const TA hb = wq * qv[9], gm = wq * qv[10], wm = wq * mu;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          if (b < a) continue;
+          const int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
+          const TA gbx = ihc * (bx ? TA(1) : TA(-1)) * phi(by, et) * phi(bz, ze);
+          const TA gby = ihc * (by ? TA(1) : TA(-1)) * phi(bx, xi) * phi(bz, ze);
+          const TA gbz = ihc * (bz ? TA(1) : TA(-1)) * phi(bx, xi) * phi(by, et);
+          TA vb[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) vb[i] = qv[3 * i] * gbx + qv[3 * i + 1] * gby + qv[3 * i + 2] * gbz;
+          const TA gg = wm * (gax * gbx + gay * gby + gaz * gbz);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[b][3 * i + k] += gm * va[i] * vb[k] - hb * vb[i] * va[k] + (i == k ? gg : TA(0));
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      if (b < a) continue;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) L.kb[(size_t)(pair8(a, b) * 9 + q) * L.NN + E] = acc[b][q];
+    }
+  }
+}
+
+// trilinear weight of coarse corner a at fine corner c of sub-element sub
+__device__ __forceinline__ float mg3_w(int sub, int c, int a) {
+  float w = 1.0f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int p = ((sub >> d) & 1) + ((c >> d) & 1);  // position in halves: 0, 1, 2
+    w *= ((a >> d) & 1) ? 0.5f * p : 1.0f - 0.5f * p;
+  }
+  return w;
+}
+
+// level l + 1 element blocks from level l, task (E, a)
+template <typename TA>
+__device__ __noinline__ void mg3_build_next(const Mg3<TA>& mg, int l) {
+  const Mg3Level<TA> F = mg.level(l), C = mg.level(l + 1);
+  const int nf = F.n, nc = C.n;
+  for (int task = threadIdx.x; task < 8 * C.NN; task += blockDim.x) {
+    const int E = task >> 3, a = task & 7;
+    const int I = E % nc, J = (E / nc) % nc, K = E / (nc * nc);
+    TA acc[8][9];
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int q = 0; q < 9; ++q) acc[b][q] = TA(0);
+    for (int sub = 0; sub < 8; ++sub) {
+      const int e = node3(nf, 2 * I + (sub & 1), 2 * J + ((sub >> 1) & 1), 2 * K + (sub >> 2));
+      for (int cc = 0; cc < 8; ++cc) {
+        const float wca = mg3_w(sub, cc, a);
+        if (wca == 0.0f) continue;
+        for (int d = 0; d < 8; ++d) {
+          TA blk[9];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) blk[3 * i + k] = mg3_kb<TA>(F, e, cc, d, i, k);
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            if (b < a) continue;
+            const float w = wca * mg3_w(sub, d, b);
+            if (w == 0.0f) continue;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) acc[b][q] += (TA)w * blk[q];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      if (b < a) continue;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) C.kb[(size_t)(pair8(a, b) * 9 + q) * C.NN + E] = acc[b][q];
+    }
+  }
+}
+
+// inverted nodal diagonal blocks of a smoothing level
+template <typename TA>
+__device__ __noinline__ void mg3_build_diag(const Mg3<TA>& mg, int l) {
+  const Mg3Level<TA> L = mg.level(l);
+  const int n = L.n;
+  for (int v = threadIdx.x; v < L.NN; v += blockDim.x) {
+    const int i = v % n, j = (v / n) % n, k = v / (n * n);
+    TA d[6] = {TA(0), TA(0), TA(0), TA(0), TA(0), TA(0)};
+    for (int a = 0; a < 8; ++a) {
+      const int E = node3(n, (i - (a & 1) + n) % n, (j - ((a >> 1) & 1) + n) % n, (k - (a >> 2) + n) % n);
+      d[0] += mg3_kb<TA>(L, E, a, a, 0, 0);
+      d[1] += mg3_kb<TA>(L, E, a, a, 0, 1);
+      d[2] += mg3_kb<TA>(L, E, a, a, 0, 2);
+      d[3] += mg3_kb<TA>(L, E, a, a, 1, 1);
+      d[4] += mg3_kb<TA>(L, E, a, a, 1, 2);
+      d[5] += mg3_kb<TA>(L, E, a, a, 2, 2);
+    }
+    const TA c00 = d[3] * d[5] - d[4] * d[4], c01 = d[2] * d[4] - d[1] * d[5], c02 = d[1] * d[4] - d[2] * d[3];
+    const TA c11 = d[0] * d[5] - d[2] * d[2], c12 = d[1] * d[2] - d[0] * d[4], c22 = d[0] * d[3] - d[1] * d[1];
+    const TA det = d[0] * c00 + d[1] * c01 + d[2] * c02;
+    const TA id = v == 0 ? TA(0) : TA(1) / det;
+    L.mi[v] = c00 * id;
+    L.mi[L.NN + v] = c01 * id;
+    L.mi[2 * L.NN + v] = c02 * id;
+    L.mi[3 * L.NN + v] = c11 * id;
+    L.mi[4 * L.NN + v] = c12 * id;
+    L.mi[5 * L.NN + v] = c22 * id;
+  }
+}
+
+// coarsest: dense pinned matrix (dof = comp * NN + node, one row per thread), then its inverse
+// by Gauss-Jordan over the block, one pivot per step, alternating between two buffers
+template <typename TA>
+__device__ __noinline__ void mg3_build_coarsest(const Mg3<TA>& mg) {
+  const Mg3Level<TA> L = mg.level(mg.levels);
+  const int n = L.n, NN = L.NN, D = 3 * NN, ld = D + 1;
+  TA* A = mg.inverse();
+  TA* B = A + (size_t)D * ld;
+  for (int row = threadIdx.x; row < D; row += blockDim.x) {
+    const int ii = row / NN, v = row % NN, i = v % n, j = (v / n) % n, k = v / (n * n);
+    for (int q = 0; q < D; ++q) A[(size_t)row * ld + q] = TA(0);
+    for (int a = 0; a < 8; ++a) {
+      const int ei = (i - (a & 1) + n) % n, ej = (j - ((a >> 1) & 1) + n) % n, ek = (k - (a >> 2) + n) % n;
+      const int E = node3(n, ei, ej, ek);
+      for (int b = 0; b < 8; ++b) {
+        const int nb = node3(n, (ei + (b & 1)) % n, (ej + ((b >> 1) & 1)) % n, (ek + (b >> 2)) % n);
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) A[(size_t)row * ld + kk * NN + nb] += mg3_kb<TA>(L, E, a, b, ii, kk);
+      }
+    }
+    if (v == 0) {
+      for (int q = 0; q < D; ++q) A[(size_t)row * ld + q] = q == row ? TA(1) : TA(0);
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) A[(size_t)row * ld + kk * NN] = TA(0);
+    }
+  }
+  __syncthreads();
+  for (int kp = 0; kp < D; ++kp) {  // SPD: no pivoting
+    const TA* Ao = (kp & 1) ? B : A;
+    TA* An = (kp & 1) ? A : B;
+    const TA ip = TA(1) / Ao[(size_t)kp * ld + kp];
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+      const int i = e / D, j = e % D;
+      const TA aik = Ao[(size_t)i * ld + kp], akj = Ao[(size_t)kp * ld + j];
+      TA v;
+      if (i == kp) v = (j == kp) ? ip : akj * ip;
+      else v = (j == kp) ? -aik * ip : Ao[(size_t)i * ld + j] - aik * akj * ip;
+      An[(size_t)i * ld + j] = v;
+    }
+    __syncthreads();
+  }
+  if (D & 1) {  // odd number of steps: the inverse ended in B
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) A[(size_t)(e / D) * ld + e % D] = B[(size_t)(e / D) * ld + e % D];
+    __syncthreads();
+  }
+}
+
+// After tangent3: all coarse levels of the current tangent.
+template <typename TA>
+__device__ void mg3_build(const Ctx3<TA>& c) {
+  mg3_build_level1<TA>(c);
+  for (int l = 1; l < c.mg.levels; ++l) {
+    __syncthreads();
+    mg3_build_next<TA>(c.mg, l);
+  }
+  __syncthreads();
+  for (int l = 1; l < c.mg.levels; ++l) mg3_build_diag<TA>(c.mg, l);
+  mg3_build_coarsest<TA>(c.mg);  // ends with a barrier
+  __syncthreads();
+}
+
+// y = K_l z at node v (gathered from the 8 elements around v; zero at the pinned node)
+template <typename TA>
+__device__ __forceinline__ void mg3_apply(const Mg3Level<TA>& L, const TA* z, int v, TA (&y)[3]) {
+  const int n = L.n, NN = L.NN, i = v % n, j = (v / n) % n, k = v / (n * n);
+  y[0] = y[1] = y[2] = TA(0);
+  if (v == 0) return;
+  for (int a = 0; a < 8; ++a) {
+    const int ei = (i - (a & 1) + n) % n, ej = (j - ((a >> 1) & 1) + n) % n, ek = (k - (a >> 2) + n) % n;
+    const int E = node3(n, ei, ej, ek);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int nb = node3(n, (ei + (b & 1)) % n, (ej + ((b >> 1) & 1)) % n, (ek + (b >> 2)) % n);
+      const TA z0 = z[nb], z1 = z[NN + nb], z2 = z[2 * NN + nb];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+        y[ii] += mg3_kb<TA>(L, E, a, b, ii, 0) * z0 + mg3_kb<TA>(L, E, a, b, ii, 1) * z1 +
+                 mg3_kb<TA>(L, E, a, b, ii, 2) * z2;
+    }
+  }
+}
+
+template <typename TA>
+__device__ __forceinline__ void mg3_smooth(const TA* mi, int NN, int v, const TA (&r)[3], TA om, TA (&z)[3]) {
+  const TA m00 = mi[v], m01 = mi[NN + v], m02 = mi[2 * NN + v], m11 = mi[3 * NN + v], m12 = mi[4 * NN + v],
+           m22 = mi[5 * NN + v];
+  z[0] = om * (m00 * r[0] + m01 * r[1] + m02 * r[2]);
+  z[1] = om * (m01 * r[0] + m11 * r[1] + m12 * r[2]);
+  z[2] = om * (m02 * r[0] + m12 * r[1] + m22 * r[2]);
+}
+
+// Full-weighting restriction to coarse node I of grid nc of the fine residual t(v) = ta[v] -
+// tb[v] (tb may be null) on grid 2 nc; zero at the pinned node.  Stores r and, for a smoothing
+// level, the pre-smoothed z.
+template <typename TA>
+__device__ __forceinline__ void mg3_restrict_smooth(const Mg3<TA>& mg, int l, const TA* ta, const TA* tb, int I) {
+  const Mg3Level<TA> C = mg.level(l);
+  const int nc = C.n, nf = 2 * nc, NNf = nf * nf * nf;
+  const int ci = I % nc, cj = (I / nc) % nc, ck = I / (nc * nc);
+  TA r[3] = {TA(0), TA(0), TA(0)};
+  if (I != 0) {
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const TA w = TA((dx ? 0.5f : 1.0f) * (dy ? 0.5f : 1.0f) * (dz ? 0.5f : 1.0f));
+          const int f = node3(nf, (2 * ci + dx + nf) % nf, (2 * cj + dy + nf) % nf, (2 * ck + dz + nf) % nf);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) r[d] += w * (tb ? ta[d * NNf + f] - tb[d * NNf + f] : ta[d * NNf + f]);
+        }
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) C.r[d * C.NN + I] = r[d];
+  if (l < mg.levels) {
+    TA z[3];
+    mg3_smooth<TA>(C.mi, C.NN, I, r, (TA)kMg3Omega, z);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) C.z[d * C.NN + I] = z[d];
+  }
+}
+
+// Trilinear prolongation of the coarse vector zc (grid nf/2) to fine node v of grid nf.
+template <typename TA>
+__device__ __forceinline__ void mg3_prolong(const TA* zc, int nf, int v, TA (&z)[3]) {
+  const int nc = nf >> 1, NNc = nc * nc * nc;
+  const int i = v % nf, j = (v / nf) % nf, k = v / (nf * nf);
+  z[0] = z[1] = z[2] = TA(0);
+  for (int p = 0; p < 8; ++p) {
+    const int px = p & 1, py = (p >> 1) & 1, pz = p >> 2;
+    if ((px && !(i & 1)) || (py && !(j & 1)) || (pz && !(k & 1))) continue;
+    const TA w = TA(((i & 1) ? 0.5f : 1.0f) * ((j & 1) ? 0.5f : 1.0f) * ((k & 1) ? 0.5f : 1.0f));
+    const int c = node3(nc, ((i >> 1) + px) % nc, ((j >> 1) + py) % nc, ((k >> 1) + pz) % nc);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) z[d] += w * zc[d * NNc + c];
+  }
+}
+
+// where the corrected z of level l ends: t of a smoothing level, z of the coarsest
+template <typename TA>
+__device__ __forceinline__ const TA* mg3_result(const Mg3<TA>& mg, int l) {
+  const Mg3Level<TA> v = mg.level(l);
+  return l == mg.levels ? v.z : v.t;
+}
+
+// Coarse part of the V-cycle (level 1 holds the restricted residual and, for a smoothing level,
+// its pre-smoothed z); result in mg3_result(mg, 1).  Two block barriers per level each way.
+template <typename TA>
+__device__ __noinline__ void mg3_coarse_cycle(const Mg3<TA>& mg) {
+  const int tid = threadIdx.x;
+  const TA om = (TA)kMg3Omega;
+  for (int l = 1; l < mg.levels; ++l) {  // descend
+    const Mg3Level<TA> v = mg.level(l);
+    for (int x = tid; x < v.NN; x += blockDim.x) {
+      TA kz[3];
+      mg3_apply<TA>(v, v.z, x, kz);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v.t[d * v.NN + x] = v.r[d * v.NN + x] - kz[d];
+    }
+    __syncthreads();
+    const Mg3Level<TA> cn = mg.level(l + 1);
+    for (int x = tid; x < cn.NN; x += blockDim.x) mg3_restrict_smooth<TA>(mg, l + 1, v.t, nullptr, x);
+    __syncthreads();
+  }
+  {  // coarsest: z = A^-1 r (rows of the pinned node: identity, z = 0 there)
+    const Mg3Level<TA> C = mg.level(mg.levels);
+    const int D = 3 * C.NN, ld = D + 1;
+    const TA* A = mg.inverse();
+    for (int row = tid; row < D; row += blockDim.x) {
+      TA zz = TA(0);
+      for (int q = 0; q < D; ++q) zz += A[(size_t)row * ld + q] * C.r[q];
+      C.z[row] = (row % C.NN == 0) ? TA(0) : zz;
+    }
+    __syncthreads();
+  }
+  for (int l = mg.levels - 1; l >= 1; --l) {  // ascend
+    const Mg3Level<TA> v = mg.level(l);
+    const TA* zc = mg3_result<TA>(mg, l + 1);
+    for (int x = tid; x < v.NN; x += blockDim.x) {
+      TA zp[3];
+      mg3_prolong<TA>(zc, v.n, x, zp);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v.z[d * v.NN + x] += zp[d];
+    }
+    __syncthreads();
+    for (int x = tid; x < v.NN; x += blockDim.x) {
+      TA kz[3], rr[3], dz[3];
+      mg3_apply<TA>(v, v.z, x, kz);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) rr[d] = v.r[d * v.NN + x] - kz[d];
+      mg3_smooth<TA>(v.mi, v.NN, x, rr, om, dz);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v.t[d * v.NN + x] = v.z[d * v.NN + x] + dz[d];
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T div3(T a, T b) {
   if constexpr (sizeof(T) == 4) {
@@ -503,6 +949,37 @@ __device__ __forceinline__ T div3(T a, T b) {
   } else {
     return a / b;
   }
+}
+
+// Fine-level part of the V-cycle: vin holds the pre-smoothed omega M^-1 r on entry and the
+// preconditioned residual on return (three fine applies per PCG iteration with the caller's).
+template <typename TA>
+__device__ __noinline__ void mg3_vcycle_fine(const Ctx3<TA>& c, const TA* r) {
+  const Mg3<TA>& mg = c.mg;
+  const int NN = c.g.NN;
+  apply3(c, 0, 0);  // vout = K vin
+  const Mg3Level<TA> L1 = mg.level(1);
+  for (int I = threadIdx.x; I < L1.NN; I += blockDim.x) mg3_restrict_smooth<TA>(mg, 1, r, c.vout, I);
+  __syncthreads();
+  mg3_coarse_cycle<TA>(mg);
+  const TA* zc = mg3_result<TA>(mg, 1);
+  for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+    TA zp[3];
+    mg3_prolong<TA>(zc, c.g.n, v, zp);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) c.vin[d * NN + v] += zp[d];
+  }
+  __syncthreads();
+  apply3(c, 0, 0);  // vout = K vin
+  for (int v = threadIdx.x; v < NN; v += blockDim.x) {
+    TA rr[3], dz[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) rr[d] = r[d * NN + v] - c.vout[d * NN + v];
+    mg3_smooth<TA>(c.sc.mi, NN, v, rr, (TA)kMg3Omega, dz);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) c.vin[d * NN + v] += dz[d];
+  }
+  __syncthreads();
 }
 
 // Chronopoulos-Gear PCG for K x = b; b given in sc.r on entry (overwritten), x in sc.x.
@@ -515,16 +992,18 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
   TA* s = c.sc.s;
   const TA* mi = c.sc.mi;
   TA* red = reinterpret_cast<TA*>(c.red);
-  auto precond_to_vin = [&]() {  // u = M^-1 r -> vin
+  auto precond_to_vin = [&]() {  // u = M^-1 r -> vin: block-Jacobi, or the multigrid V-cycle
+    const TA om = c.mg.levels ? (TA)kMg3Omega : TA(1);
     for (int v = threadIdx.x; v < NN; v += blockDim.x) {
       const TA r0 = r[v], r1 = r[NN + v], r2 = r[2 * NN + v];
       const TA m00 = mi[v], m01 = mi[NN + v], m02 = mi[2 * NN + v], m11 = mi[3 * NN + v], m12 = mi[4 * NN + v],
                m22 = mi[5 * NN + v];
-      c.vin[v] = m00 * r0 + m01 * r1 + m02 * r2;
-      c.vin[NN + v] = m01 * r0 + m11 * r1 + m12 * r2;
-      c.vin[2 * NN + v] = m02 * r0 + m12 * r1 + m22 * r2;
+      c.vin[v] = om * (m00 * r0 + m01 * r1 + m02 * r2);
+      c.vin[NN + v] = om * (m01 * r0 + m11 * r1 + m12 * r2);
+      c.vin[2 * NN + v] = om * (m02 * r0 + m12 * r1 + m22 * r2);
     }
     __syncthreads();
+    if (c.mg.levels) mg3_vcycle_fine<TA>(c, r);
   };
   auto dots = [&](TA& gam, TA& del) {
     TA g = TA(0), d = TA(0);
@@ -614,6 +1093,9 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
   double* misc = lame_s + 2 * kMaxPhase;
   c.lame = lame_s;
   c.sc = scratch3_layout<TA>(gscr, NN);
+  c.mg.levels = a.mg ? mg3_levels(n) : 0;
+  c.mg.n = n;
+  c.mg.base = c.sc.mg;
   if (threadIdx.x < 2 * kMaxPhase) lame_s[threadIdx.x] = a.rve_lame[(size_t)rv * 2 * kMaxPhase + threadIdx.x];
 #pragma unroll
   for (int k = 0; k < 9; ++k) c.Fb[k] = a.F[(size_t)qp * 9 + k];
@@ -682,6 +1164,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
         break;
       }
       tangent3<TA, false>(c, w, nullptr);
+      if (c.mg.levels) mg3_build<TA>(c);
       int pst = kStatusOk;
       cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
       if (pst == kStatusPcgBreakdown) {
@@ -733,6 +1216,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
 #pragma unroll
     for (int k = 0; k < 45; ++k) As[k] = 0.0;
     tangent3<TA, true>(c, w, As);
+    if (c.mg.levels) mg3_build<TA>(c);
     // <A>: 45 FP64 sums in three reductions of 15
     for (int part = 0; part < 3; ++part) block_sum_n<double>(As + 15 * part, 15, c.red);
     // right-hand sides L_c (c = 3k + L) stored [c][3][NN]

@@ -90,3 +90,26 @@ def test_failed_start_retried_by_load_continuation(precision):
     ref = rve.solve(F[0], rtol=1e-14, atol=1e-16, stages=4)
     check(on, [ref], TOL[precision])
     assert on["iters"][0][0] > 4  # Newton iterations summed over the first try and the four increments
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multigrid_and_block_jacobi_agree_3d(precision):
+    """3D: both preconditioners reach the oracle's P and A; the multigrid V-cycle (n = 8: coarse
+    levels 4, 2; n = 12: 6, 3) needs far fewer PCG iterations; n = 10 has no hierarchy."""
+    sizes = [8, 12, 10]
+    u = synth.uniform(641, np.arange(len(sizes)), 5)
+    phases = [synth.sphere_rve(n, 1, 0.15 + 0.1 * u[k, 3], [u[k, :3]]) for k, n in enumerate(sizes)]
+    E = [[1.0, 10.0]] * len(sizes)
+    nu = [[0.3, 0.3]] * len(sizes)
+    Fs = synth.random_F(642, len(sizes), 3, 0.08)
+    opts = STRICT if precision == "fp64" else {}
+    mg = gpu_batch(3, precision, sizes, phases, E, nu, np.arange(len(sizes)), Fs, precond=1, **opts)
+    bj = gpu_batch(3, precision, sizes, phases, E, nu, np.arange(len(sizes)), Fs, precond=0, **opts)
+    refs = [PeriodicRVE(n, 3, phases[k], E[k], nu[k]).solve(Fs[k], rtol=1e-14, atol=1e-16)
+            for k, n in enumerate(sizes)]
+    check(mg, refs, TOL[precision])
+    check(bj, refs, TOL[precision])
+    for q in (0, 1):
+        assert mg["iters"][q][1] < 0.3 * bj["iters"][q][1], (sizes[q], mg["iters"][q], bj["iters"][q])
+        assert mg["iters"][q][2] < 0.3 * bj["iters"][q][2], (sizes[q], mg["iters"][q], bj["iters"][q])
+    assert mg["iters"][2][1] == bj["iters"][2][1]
