@@ -53,6 +53,13 @@ FP64_FLOP_PER_ELEMENT_RESIDUAL_3D = 2640.0   # Hex8: 8 Gauss points x (grad, F^-
 FP32_FLOP_PER_ELEMENT_TANGENT_3D = 4200.0    # Gauss-point data + 3x3 diagonal blocks
 FP32_FLOP_PER_ELEMENT_APPLY_3D = 4000.0      # matrix-free apply: grad, dP = A:dF, nodal scatter
 FP32_FLOP_PER_NODE_PCG_ITER_3D = 30.0        # preconditioner + vector updates + dots
+# 3D multigrid, per fine element: V-cycle per PCG iteration = two more fine applies (2 x 4000),
+# level-1 gathers (2 x 1152 flop per coarse node / 8), deeper levels, smoothing, restriction and
+# prolongation; per tangent build the level-1 element blocks integrated over the 64 fine Gauss
+# points of each coarse element (3312 flop per Gauss point, 212k per coarse element, 26.5k per
+# fine element), deeper levels (2.3k) and the coarsest inverse (<= 0.6k)
+FP32_FLOP_PER_ELEMENT_MG_ITER_3D = 8400.0
+FP32_FLOP_PER_ELEMENT_MG_BUILD_3D = 29000.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
 
@@ -65,6 +72,8 @@ def workload_config(step_index):
                             f"stiffness ratio 10), neo-Hookean, mixed FP32/FP64, uneven batch in one persistent "
                             f"launch, macro iteration 1 of load step {step_index}/{N_STEPS_C3} (uniaxial to 20%)",
                 "n_qp": MACRO ** 3 * 8, "rve_grid": "8/12/16 mixed", "load_step": step_index,
+                "rve_preconditioner": ("multigrid V(1,1), Galerkin levels n/2 .. 2 or 3" if _SIZE.get("precond", "mg") == "mg"
+                                       else "block-Jacobi"),
                 "l2": "flushed (256 MB write) between timed steps"}
     W = _SIZE["world"]
     cfg = {"workload": f"2D plane-strain FE-HMM macro {MACRO}x{MACRO * W} Q1 ({MACRO * MACRO * W * 4} qps), "
@@ -166,14 +175,26 @@ def macro_affine_u(F):
     return (X @ (F - np.eye(d)).T).reshape(-1)
 
 
-def flops_3d(p, iters):
+def mg3_levels(n):
+    """Coarse levels of the 3D multigrid for grid n (0: block-Jacobi), as the kernel decides."""
+    l, m = 0, n
+    while m > 3 and m % 2 == 0:
+        m //= 2
+        l += 1
+    return l if (m <= 3 and l >= 1) else 0
+
+
+def flops_3d(p, iters, mg=False):
     """FP64 and FP32 algorithmic flops of one 3D batch solve from the per-qp iteration counts."""
-    el = np.array([int(p.rve_n[r]) ** 3 for r in p.qp_rve], dtype=np.float64)
+    ns = np.array([int(p.rve_n[r]) for r in p.qp_rve])
+    el = ns.astype(np.float64) ** 3
+    on = np.array([mg and mg3_levels(int(n)) > 0 for n in ns], dtype=np.float64)
     newton = iters[:, 0].astype(np.float64)
     cg = iters[:, 1].astype(np.float64) + iters[:, 2].astype(np.float64)
     f64 = ((newton + 1) * FP64_FLOP_PER_ELEMENT_RESIDUAL_3D * el).sum()
-    f32 = ((newton + 1) * FP32_FLOP_PER_ELEMENT_TANGENT_3D * el
-           + (cg + 9) * (FP32_FLOP_PER_ELEMENT_APPLY_3D + FP32_FLOP_PER_NODE_PCG_ITER_3D) * el).sum()
+    f32 = ((newton + 1) * (FP32_FLOP_PER_ELEMENT_TANGENT_3D + on * FP32_FLOP_PER_ELEMENT_MG_BUILD_3D) * el
+           + (cg + 9) * (FP32_FLOP_PER_ELEMENT_APPLY_3D + FP32_FLOP_PER_NODE_PCG_ITER_3D) * el
+           + cg * on * FP32_FLOP_PER_ELEMENT_MG_ITER_3D * el).sum()
     return f64, f32
 
 
@@ -330,7 +351,8 @@ def run_gpu(args):
     value = n_total / (t_step / args.steps)
     dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve[mine]], dtype=np.float64)
     dof_iter = float((dofs * iters[:, 0].astype(np.float64)).sum()) * world / (t_step / args.steps)
-    f64, f32 = flops_2d(RVE_N, iters, args.precond == "mg") if d == 2 else flops_3d(p, iters)
+    f64, f32 = (flops_2d(RVE_N, iters, args.precond == "mg") if d == 2
+                else flops_3d(p, iters, args.precond == "mg"))
     t_rve = statistics.mean(rve_ms) / 1e3
     ach_eq = (f32 + f64 * FP32_PEAK_TFLOPS / FP64_PEAK_TFLOPS) / t_rve / 1e12
     out = {

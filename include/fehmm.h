@@ -99,12 +99,13 @@ typedef struct {
                            warm-started from the last, each allowed max(max_newton, 25)
                            Newton iterations); 0 or 1 turns the retry off.  The status is that
                            of the retried solve; the Newton count adds up all stages. */
-  int precond;          /* FEHMM_PRECOND_MULTIGRID (default): in 2D, grids n = 2^k m with
-                           m <= 4 and n >= 6 use a geometric V(1,1)-cycle with Galerkin
-                           coarse levels and block-Jacobi smoothing; other grids, 3D and
-                           FEHMM_PRECOND_BLOCK_JACOBI use block-Jacobi (inverted nodal d x d
-                           blocks).  The choice changes iteration counts, not the tolerances
-                           the solves meet. */
+  int precond;          /* FEHMM_PRECOND_MULTIGRID (default): grids whose halving ends at
+                           m nodes per axis (2D: n = 2^k m, m <= 4, n >= 6; 3D: m <= 3,
+                           n >= 4) use a geometric V(1,1)-cycle with Galerkin coarse levels,
+                           damped block-Jacobi smoothing and an exact coarsest solve; other
+                           grids and FEHMM_PRECOND_BLOCK_JACOBI use block-Jacobi (inverted
+                           nodal d x d blocks).  The choice changes iteration counts, not the
+                           tolerances the solves meet. */
 } fehmm_options;
 
 /* Fill `opt` with defaults for dim (2|3) and precision. */
