@@ -112,4 +112,6 @@ def test_multigrid_and_block_jacobi_agree_3d(precision):
     for q in (0, 1):
         assert mg["iters"][q][1] < 0.3 * bj["iters"][q][1], (sizes[q], mg["iters"][q], bj["iters"][q])
         assert mg["iters"][q][2] < 0.3 * bj["iters"][q][2], (sizes[q], mg["iters"][q], bj["iters"][q])
-    assert mg["iters"][2][1] == bj["iters"][2][1]
+    # n = 10 runs block-Jacobi either way; the 3D apply sums with float atomics, so iteration
+    # counts may differ by the order of the sums
+    assert abs(int(mg["iters"][2][1]) - int(bj["iters"][2][1])) <= max(2, 0.02 * bj["iters"][2][1])
