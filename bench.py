@@ -192,7 +192,8 @@ def flops_3d(p, iters, mg=False):
     newton = iters[:, 0].astype(np.float64)
     cg = iters[:, 1].astype(np.float64) + iters[:, 2].astype(np.float64)
     f64 = ((newton + 1) * FP64_FLOP_PER_ELEMENT_RESIDUAL_3D * el).sum()
-    f32 = ((newton + 1) * (FP32_FLOP_PER_ELEMENT_TANGENT_3D + on * FP32_FLOP_PER_ELEMENT_MG_BUILD_3D) * el
+    # the coarse levels are built at the first Newton iteration and for the tangent transfer
+    f32 = ((newton + 1) * FP32_FLOP_PER_ELEMENT_TANGENT_3D * el + 2 * on * FP32_FLOP_PER_ELEMENT_MG_BUILD_3D * el
            + (cg + 9) * (FP32_FLOP_PER_ELEMENT_APPLY_3D + FP32_FLOP_PER_NODE_PCG_ITER_3D) * el
            + cg * on * FP32_FLOP_PER_ELEMENT_MG_ITER_3D * el).sum()
     return f64, f32

@@ -1168,7 +1168,11 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
         break;
       }
       tangent3<TA, false>(c, w, nullptr);
-      if (c.mg.levels) mg3_build<TA>(c);
+      // The coarse levels are built on the first Newton iteration of a solve (or continuation
+      // stage) and reused by the later ones: a V-cycle with coarse operators of a nearby tangent,
+      // current fine smoothing and current fine residuals is still symmetric positive definite,
+      // only slightly less effective.  The tangent transfer rebuilds them at the converged state.
+      if (c.mg.levels && it == 0) mg3_build<TA>(c);
       int pst = kStatusOk;
       cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
       if (pst == kStatusPcgBreakdown) {
