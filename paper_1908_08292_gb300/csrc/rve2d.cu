@@ -955,7 +955,10 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
   block_sum2<TA>(gamma, delta, red1);
   const TA gamma0 = gamma;
   int it = 0;
-  if (gamma0 > TA(0)) {
+  // a non-finite preconditioned residual (e.g. a multigrid coarse inverse of an indefinite
+  // tangent) is a breakdown, not a converged zero correction
+  if (!isfinite(gamma0)) *status = kStatusPcgBreakdown;
+  if (gamma0 > TA(0) && isfinite(gamma0)) {
     if (!(delta > TA(0))) {
       if (truncate && delta < TA(0)) {
         const TA a0 = cg_div<TA>(gamma, -delta);

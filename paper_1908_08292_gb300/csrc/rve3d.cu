@@ -1028,6 +1028,11 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
   dots(gamma, delta);
   const TA gamma0 = gamma;
   int it = 0;
+  if (!isfinite(gamma0)) {  // non-finite preconditioned residual: a breakdown
+    *status = kStatusPcgBreakdown;
+    __syncthreads();
+    return 0;
+  }
   if (!(gamma0 > TA(0))) return 0;
   if (!(delta > TA(0))) {
     if (truncate && delta < TA(0)) {
