@@ -89,3 +89,53 @@ def hooke(lam, mu, d):
     """Isotropic linear elasticity tensor lam 1x1 + 2 mu I^sym (textbook small-strain law)."""
     I = np.eye(d)
     return lam * np.einsum("ij,kl->ijkl", I, I) + mu * (np.einsum("ik,jl->ijkl", I, I) + np.einsum("il,jk->ijkl", I, I))
+
+
+# ------------------------------------------------------------------ St. Venant-Kirchhoff
+# The paper's second material case (Sec. 6, Table of material parameters, "linear elasticity
+# along with geometrical nonlinearity"): the linear elastic law written in the Green-Lagrange
+# strain E = (C - I)/2 and the second Piola-Kirchhoff stress,
+#   psi = lam/2 (tr E)^2 + mu E:E,  S = lam tr(E) I + 2 mu E,  CC = lam I x I + 2 mu I^sym.
+# Plane strain in 2D: E_33 = 0 (F_33 = 1), so tr E = E_11 + E_22.
+
+def green_lagrange(F):
+    F = np.asarray(F, dtype=np.float64)
+    d = F.shape[-1]
+    return 0.5 * (np.swapaxes(F, -1, -2) @ F - np.eye(d))
+
+
+def svk_psi(F, lam, mu):
+    E = green_lagrange(F)
+    trE = np.trace(E, axis1=-2, axis2=-1)
+    return lam / 2.0 * trE ** 2 + mu * np.einsum("...ij,...ij->...", E, E)
+
+
+def svk_S(F, lam, mu):
+    E = green_lagrange(F)
+    d = E.shape[-1]
+    trE = np.trace(E, axis1=-2, axis2=-1)[..., None, None]
+    lam = np.asarray(lam)[..., None, None]
+    mu = np.asarray(mu)[..., None, None]
+    return lam * trE * np.eye(d) + 2.0 * mu * E
+
+
+def svk_P(F, lam, mu):
+    return np.asarray(F, dtype=np.float64) @ svk_S(F, lam, mu)
+
+
+def svk_A(F, lam, mu):
+    """dP_iJ/dF_kL = delta_ik S_JL + F_iI F_kK CC_IJKL with the constant CC of the law."""
+    F = np.asarray(F, dtype=np.float64)
+    d = F.shape[-1]
+    S = svk_S(F, lam, mu)
+    lam_b = np.asarray(lam)[..., None, None, None, None]
+    mu_b = np.asarray(mu)[..., None, None, None, None]
+    I = np.eye(d)
+    CC = lam_b * np.einsum("IJ,KL->IJKL", I, I) + mu_b * (np.einsum("IK,JL->IJKL", I, I) + np.einsum("IL,JK->IJKL", I, I))
+    geo = np.einsum("ik,...JL->...iJkL", I, S)
+    return geo + np.einsum("...iI,...kK,...IJKL->...iJkL", F, F, CC)
+
+
+# Constitutive laws by name: (psi, P, A).  "nh" is the paper's neo-Hookean law (Eq.
+# NH-free-energy), "svk" the St. Venant-Kirchhoff law above.
+LAWS = {"nh": (psi, P_of_F, A_of_F), "svk": (svk_psi, svk_P, svk_A)}

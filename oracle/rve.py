@@ -77,8 +77,10 @@ def shape_and_grad(d, xi, h):
 class PeriodicRVE:
     """One microstructure on a periodic n^d grid with per-element phases."""
 
-    def __init__(self, n, dim, phase, E, nu):
+    def __init__(self, n, dim, phase, E, nu, law="nh"):
         self.n, self.d = int(n), int(dim)
+        self.law = law
+        self._psi, self._P, self._A = mat.LAWS[law]
         d, n = self.d, self.n
         self.phase = np.asarray(phase, dtype=np.int64).reshape(-1)
         assert self.phase.size == n ** d
@@ -115,7 +117,7 @@ class PeriodicRVE:
         """R_a = sum_e sum_qp wt detJ P N_a,J  (flattened, n_dof)."""
         F = self.F_at_qps(w, Fbar)
         lam, mu = self._lam_mu()
-        P = mat.P_of_F(F, lam, mu)
+        P = self._P(F, lam, mu)
         Re = self.wdet * np.einsum("eqiJ,qaJ->eai", P, self.G)
         R = np.zeros((self.n_nodes, self.d))
         np.add.at(R, self.conn, Re)
@@ -125,7 +127,7 @@ class PeriodicRVE:
         """Element matrices k_e[(a,i),(b,k)] = sum_qp wt detJ N_a,J A_iJkL N_b,L."""
         F = self.F_at_qps(w, Fbar)
         lam, mu = self._lam_mu()
-        A = mat.A_of_F(F, lam, mu)
+        A = self._A(F, lam, mu)
         ke = self.wdet * np.einsum("qaJ,eqiJkL,qbL->eaibk", self.G, A, self.G)
         nen = self.G.shape[1]
         return ke.reshape(-1, nen * self.d, nen * self.d), A
@@ -149,8 +151,16 @@ class PeriodicRVE:
         F = self.F_at_qps(w, Fbar)
         C = np.swapaxes(F, -1, -2) @ F
         lam, mu = self._lam_mu()
-        S = mat.S_of_C(C, lam, mu)
-        CC = mat.CC_of_C(C, lam, mu)
+        if self.law == "svk":
+            S = mat.svk_S(F, lam, mu)
+            I = np.eye(d)
+            lb, mb = lam[..., None, None, None, None], mu[..., None, None, None, None]
+            CC = np.broadcast_to(lb * np.einsum("IJ,KL->IJKL", I, I)
+                                 + mb * (np.einsum("IK,JL->IJKL", I, I) + np.einsum("IL,JK->IJKL", I, I)),
+                                 F.shape[:2] + (d, d, d, d))
+        else:
+            S = mat.S_of_C(C, lam, mu)
+            CC = mat.CC_of_C(C, lam, mu)
         pairs = [(0, 0), (1, 1), (0, 1)] if d == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2)]
         nv = len(pairs)
         Cv = np.zeros(CC.shape[:2] + (nv, nv))
@@ -215,9 +225,9 @@ class PeriodicRVE:
         """<P>, <F>, <psi> and <A> over the cell (Eq. Average-of-P-and-F); |Omega| = 1."""
         F = self.F_at_qps(w, Fbar)
         lam, mu = self._lam_mu()
-        P = mat.P_of_F(F, lam, mu)
-        A = mat.A_of_F(F, lam, mu)
-        W = mat.psi(F, lam, mu)
+        P = self._P(F, lam, mu)
+        A = self._A(F, lam, mu)
+        W = self._psi(F, lam, mu)
         s = self.wdet / self.volume
         return (s * P.sum(axis=(0, 1)), s * F.sum(axis=(0, 1)), s * W.sum(), s * A.sum(axis=(0, 1)))
 
@@ -225,7 +235,7 @@ class PeriodicRVE:
         """L[(a,i),(k,L)] = sum wt detJ N_a,J A_iJkL: derivative of R with respect to Fbar."""
         F = self.F_at_qps(w, Fbar)
         lam, mu = self._lam_mu()
-        A = mat.A_of_F(F, lam, mu)
+        A = self._A(F, lam, mu)
         Le = self.wdet * np.einsum("qaJ,eqiJkL->eaikL", self.G, A)
         L = np.zeros((self.n_nodes, self.d, self.d, self.d))
         np.add.at(L, self.conn, Le)
