@@ -72,8 +72,6 @@ def workload_config(step_index):
                             f"stiffness ratio 10), neo-Hookean, mixed FP32/FP64, uneven batch in one persistent "
                             f"launch, macro iteration 1 of load step {step_index}/{N_STEPS_C3} (uniaxial to 20%)",
                 "n_qp": MACRO ** 3 * 8, "rve_grid": "8/12/16 mixed", "load_step": step_index,
-                "rve_preconditioner": ("multigrid V(1,1), Galerkin levels n/2 .. 2 or 3" if _SIZE.get("precond", "mg") == "mg"
-                                       else "block-Jacobi"),
                 "l2": "flushed (256 MB write) between timed steps"}
     W = _SIZE["world"]
     cfg = {"workload": f"2D plane-strain FE-HMM macro {MACRO}x{MACRO * W} Q1 ({MACRO * MACRO * W * 4} qps), "
@@ -81,9 +79,7 @@ def workload_config(step_index):
                        f"E ratio log-U[5,50]), neo-Hookean, mixed FP32/FP64, macro iteration 1 of load step "
                        f"{step_index}/{N_STEPS} (biaxial 30% + shear 0.3)",
            "n_qp": MACRO * MACRO * W * 4, "rve_grid": RVE_N, "micro_dofs_per_rve": 2 * RVE_N * RVE_N,
-           "load_step": step_index, "l2": "flushed (256 MB write) between timed steps",
-           "rve_preconditioner": ("multigrid V(1,1), Galerkin levels 16/8/4" if _SIZE.get("precond", "mg") == "mg"
-                                  else "block-Jacobi")}
+           "load_step": step_index, "l2": "flushed (256 MB write) between timed steps"}
     if W > 1:
         cfg["parallelism"] = (f"dp{W}: macro elements in {W} contiguous blocks balanced by RVE dofs, one per rank; "
                               "all-reduce of f and K, macro solve on rank 0, broadcast of du")
@@ -362,6 +358,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed: FP64 residual/sums, FP32 tangent/PCG)",
         "data": "synthetic (seeded generator, config-2 shapes)", "config": workload_config(args.step_index),
         "micro_dof_newton_iter_per_s": dof_iter,
+        "rve_preconditioner": ("multigrid V(1,1) with Galerkin coarse levels" if args.precond == "mg"
+                               else "block-Jacobi"),
         "rve_status_ok": ok, "newton_iters_mean": float(iters[:, 0].mean()),
         "pcg_iters_per_rve_mean": float(iters[:, 1].mean()), "transfer_pcg_iters_per_rve_mean": float(iters[:, 2].mean()),
         "phase_ms": {"macro_qp_F": statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)),
