@@ -20,7 +20,9 @@
 //    REGISTERS, where it stays for the whole PCG; the PCG exchanges only the search
 //    direction through shared memory.  FP64 mode (TA = double) keeps the staged element
 //    tangents and the stencil in a per-block global scratch area (L2 resident).
-//  * Block-Jacobi preconditioner (inverted 2x2 nodal diagonal blocks).
+//  * Preconditioner: geometric multigrid V(1,1)-cycle with Galerkin coarse levels (grids
+//    n = 2^k m, m <= 4; a separate kernel instantiation), else block-Jacobi (inverted 2x2
+//    nodal diagonal blocks).
 //  * Newton iterations stop on the FP64 2-norm of the residual; PCG inner products are
 //    summed in TA: at GB300's FP64:FP32 rate of about 1:62 an FP64 block reduction per CG
 //    iteration would cost more than the stencil apply.

@@ -18,8 +18,10 @@
 //    F^-T, hb and lam J^2 (11 values); the apply computes dF = Grad p from edge differences,
 //    dP = mu dF - hb Fit dF^T Fit + gm (Fit:dF) Fit and adds the element's nodal results to
 //    shared memory with float atomics.
-//  * Block-Jacobi with the 3x3 nodal diagonal blocks; PCG in the single-reduction form of
-//    Chronopoulos and Gear; truncated on negative curvature for Newton corrections.
+//  * Preconditioner: geometric multigrid V(1,1)-cycle with Galerkin coarse levels where the
+//    grid halves down to 2 or 3 nodes per axis, else block-Jacobi with the 3x3 nodal diagonal
+//    blocks; PCG in the single-reduction form of Chronopoulos and Gear; truncated on negative
+//    curvature for Newton corrections.
 //  * Tangent transfer: L_c = apply of the element operator to the constant gradient E_c (the
 //    affine field), 9 PCG solves X_c = -K^-1 L_c, Abar = <A> + sym(L^T X), all sums in FP64.
 #include <cuda_runtime.h>
