@@ -66,7 +66,9 @@ enum {
   FEHMM_RVE_J_NONPOS = 2,      /* det F <= 0 at some Gauss point (ln J undefined) */
   FEHMM_RVE_PCG_BREAKDOWN = 3, /* p^T K p <= 0 in the linear solver (tangent not SPD) */
   FEHMM_RVE_NONFINITE = 4,     /* NaN/Inf in the residual */
-  FEHMM_RVE_PCG_CAP = 5        /* the tangent-transfer solve hit its iteration cap */
+  FEHMM_RVE_PCG_CAP = 5,       /* the tangent-transfer solve hit its iteration cap */
+  FEHMM_RVE_BAD_PHASE = 7      /* a phase id >= 4 in a device-supplied phase map (no-allocation
+                                  entry point): nothing is solved, P/A/w are left unchanged */
 };
 
 /* fehmm_rve_solve flags */
@@ -306,7 +308,8 @@ const char* fehmm_status_str(int code);
  *   n_qp          number of quadrature points (RVE solves)
  *   grid_n        elements per axis of every RVE: even, 2..16; larger -> FEHMM_ERR_TOO_LARGE
  *   phase_per_qp  1: phase holds one map per qp; 0: one map shared by all
- *   phase   device uint8 [phase_per_qp ? n_qp : 1][grid_n*grid_n], phase ids < 4
+ *   phase   device uint8 [phase_per_qp ? n_qp : 1][grid_n*grid_n], phase ids < 4 (a point
+ *           whose map holds a larger id gets status FEHMM_RVE_BAD_PHASE and is not solved)
  *   lame    device double [phase_per_qp ? n_qp : 1][4][2]: (lambda, mu) of each phase
  *   w       device double [n_qp][grid_n*grid_n][2]: fluctuation start values in, results
  *           out (the value at node 0 is taken as zero)

@@ -20,7 +20,8 @@ namespace fehmm {
 constexpr int kMaxPhase = 4;
 constexpr int kStatusOk = 0, kStatusNewtonCap = 1, kStatusJNonPos = 2, kStatusPcgBreakdown = 3,
               kStatusNonFinite = 4, kStatusPcgCap = 5,
-              kStatusNegCurv = 6;  // internal: truncated Newton-correction PCG
+              kStatusNegCurv = 6,  // internal: truncated Newton-correction PCG
+              kStatusBadPhase = 7;  // a device-supplied phase id >= kMaxPhase (nothing solved)
 constexpr int kFlagNoTangent = 1, kFlagFromCommitted = 2, kFlagEnergy = 4;
 // Newton globalisation: after an update that makes det F <= 0 somewhere (or the residual
 // non-finite) the step is halved, up to this many times, before the RVE is reported failed.
@@ -64,6 +65,35 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* buf) {
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = warp_sum(lane < nw ? buf[k * 32 + lane] : T(0));
+}
+
+// Two inner products summed over a block of 16 warps, the block-level sum in FP64: each thread's
+// partial and the warp's shuffle tree stay in T (FP32 in mixed mode), lane 0 of every warp
+// stores its warp sum as a double, and warp 0 adds the 16 warp sums of each product in FP64
+// (lanes 0-15 the first, lanes 16-31 the second, a 4-level shuffle tree in a fixed order, so
+// every launch sums identically) and broadcasts them.  Two barriers.  buf: 34 doubles of shared
+// memory; consecutive calls may reuse it (the second barrier orders every read of a call before
+// the next call's writes).
+template <typename T>
+__device__ __forceinline__ void block_dot2_fp64(T a, T b, double* buf, double& sa, double& sb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane == 0) {
+    buf[warp] = (double)a;
+    buf[16 + warp] = (double)b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    double v = (lane & 15) < nw ? buf[lane] : 0.0;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((lane & 15) == 0) buf[32 + (lane >> 4)] = v;
+  }
+  __syncthreads();
+  sa = buf[32];
+  sb = buf[33];
 }
 
 // Lame constants from (E, nu), as in the paper's material table (Sec. 6).

@@ -28,6 +28,9 @@ constexpr int kRowsPerBlock = kSolveThreads / kRowLanes;  // 32
 
 // Sum (a, b) over the grid: block sums -> partial[2*block], grid barrier, every block adds the
 // partials in index order (warp 0, fixed shuffle tree), so all blocks get identical totals.
+// Consecutive calls must use alternate partial buffers: a block may write the next call's
+// partials while a slower block still reads this call's, and only a grid barrier of the call
+// in between (every call has one) orders the reads of call k before the writes of call k + 2.
 __device__ void grid_sum2(double& a, double& b, double* partial, double (*sbuf)[2], cg::grid_group& grid) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -111,7 +114,13 @@ __global__ void __launch_bounds__(kSolveThreads) macro_pcg_kernel(const MacroSol
   double* p = w + n;
   double* s = p + n;
   double* dinv = s + n;
-  double* partial = dinv + n;  // [2 * gridDim.x]
+  double* partials = dinv + n;  // two buffers of [2 * gridDim.x], alternated between grid sums
+  int parity = 0;
+  auto next_partial = [&]() {
+    double* buf = partials + (size_t)parity * 2 * gridDim.x;
+    parity ^= 1;
+    return buf;
+  };
   // Jacobi diagonal, r = -f on free rows, u = M^-1 r
   double ff = 0.0, ru = 0.0;
   for (int i = tid; i < n; i += stride) {
@@ -130,14 +139,14 @@ __global__ void __launch_bounds__(kSolveThreads) macro_pcg_kernel(const MacroSol
     ff = fma(ri, ri, ff);
     ru = fma(ri, ri * di, ru);
   }
-  grid_sum2(ff, ru, partial, sbuf, grid);  // its grid barrier also publishes u and dinv
+  grid_sum2(ff, ru, next_partial(), sbuf, grid);  // its grid barrier also publishes u and dinv
   if (tid == 0) a.out[0] = sqrt(ff);
   double gamma = ru;
   const double stop = a.rtol * a.rtol * gamma;
   int it = 0, status = 0;
   if (gamma > 0.0) {
     double delta = spmv_rows(a, dinv, u, w, n), unused = 0.0;
-    grid_sum2(delta, unused, partial, sbuf, grid);
+    grid_sum2(delta, unused, next_partial(), sbuf, grid);
     double alpha = gamma / delta, beta = 0.0;
     if (!(delta > 0.0)) status = 2;
     while (status == 0) {
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(kSolveThreads) macro_pcg_kernel(const MacroSol
       ++it;
       grid.sync();  // u complete before the product
       double d = spmv_rows(a, dinv, u, w, n);
-      grid_sum2(g, d, partial, sbuf, grid);
+      grid_sum2(g, d, next_partial(), sbuf, grid);
       if (g <= stop) break;
       if (it >= a.max_it) {
         status = 1;
@@ -182,7 +191,7 @@ __global__ void __launch_bounds__(kSolveThreads) macro_pcg_kernel(const MacroSol
 
 }  // namespace
 
-size_t macro_solve_work_doubles(int n, int blocks) { return 6 * (size_t)n + 2 * (size_t)blocks; }
+size_t macro_solve_work_doubles(int n, int blocks) { return 6 * (size_t)n + 4 * (size_t)blocks; }
 
 // One block per 32 rows (one pass of the product), at most one per SM.
 int macro_solve_blocks(int num_sms, long long n_rows) {

@@ -118,7 +118,16 @@ extern "C" int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_pe
   a.scratch_stride = 72LL * a.nn_max;
   a.flags = A ? 0 : kFlagNoTangent;
   // the shared work counter keeps the previous call's value: clear it on this stream
-  if (cudaMemsetAsync(slots.queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;
+  // (a failed call is reported as FEHMM_ERR_CUDA with the runtime's last-error state
+  // cleared, so that the caller's next CUDA call does not see it)
+  if (cudaMemsetAsync(slots.queue, 0, sizeof(int32_t), s) != cudaSuccess) {
+    cudaGetLastError();
+    return FEHMM_ERR_CUDA;
+  }
   const int blocks = std::min(std::min(n_qp, slots.num_sms), kNoallocMaxBlocks);
-  return rve2d_launch_fixed_fp64(a, blocks, s) == cudaSuccess ? FEHMM_OK : FEHMM_ERR_CUDA;
+  if (rve2d_launch_fixed_fp64(a, blocks, s) != cudaSuccess) {
+    cudaGetLastError();
+    return FEHMM_ERR_CUDA;
+  }
+  return FEHMM_OK;
 }

@@ -997,7 +997,6 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
   TA* p = c.sc.p;
   TA* s = c.sc.s;
   const TA* mi = c.sc.mi;
-  TA* red = reinterpret_cast<TA*>(c.red);
   auto precond_to_vin = [&]() {  // u = M^-1 r -> vin: block-Jacobi, or the multigrid V-cycle
     const TA om = c.mg.levels ? (TA)kMg3Omega : TA(1);
     for (int v = threadIdx.x; v < NN; v += blockDim.x) {
@@ -1011,32 +1010,32 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
     __syncthreads();
     if (c.mg.levels) mg3_vcycle_fine<TA>(c, r);
   };
-  auto dots = [&](TA& gam, TA& del) {
+  // inner products: per thread and per warp in TA, over the block in FP64 (block_dot2_fp64); the
+  // stopping test compares the FP64 sums, the step scalars are formed in TA from them
+  auto dots = [&](double& gam, double& del) {
     TA g = TA(0), d = TA(0);
     for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
       g += r[v] * c.vin[v];
       d += c.vout[v] * c.vin[v];
     }
-    TA vv[2] = {g, d};
-    block_sum_n<TA>(vv, 2, red);
-    gam = vv[0];
-    del = vv[1];
+    block_dot2_fp64<TA>(g, d, c.red + 2 * 512 - 64, gam, del);
   };
   for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) x[v] = TA(0);
   *status = kStatusOk;
   precond_to_vin();
   apply3(c, 0, 0);
-  TA gamma, delta;
-  dots(gamma, delta);
-  const TA gamma0 = gamma;
+  double gd, dd;
+  dots(gd, dd);
+  TA gamma = (TA)gd, delta = (TA)dd;
+  const double gamma0 = gd;
   int it = 0;
   if (!isfinite(gamma0)) {  // non-finite preconditioned residual: a breakdown
     *status = kStatusPcgBreakdown;
     __syncthreads();
     return 0;
   }
-  if (!(gamma0 > TA(0))) return 0;
-  if (!(delta > TA(0))) {
+  if (!(gamma0 > 0.0)) return 0;
+  if (!(dd > 0.0)) {
     if (truncate && delta < TA(0)) {
       const TA a0 = div3(gamma, -delta);
       for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) x[v] = a0 * c.vin[v];
@@ -1047,7 +1046,7 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
     __syncthreads();
     return 0;
   }
-  const TA stop = rtol * rtol * gamma0;
+  const double stop = (double)rtol * (double)rtol * gamma0;
   TA alpha = div3(gamma, delta), beta = TA(0);
   for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
     p[v] = c.vin[v];
@@ -1065,10 +1064,11 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
     __syncthreads();
     precond_to_vin();
     apply3(c, 0, 0);
-    TA gn, dn;
-    dots(gn, dn);
+    double gnd, dnd;
+    dots(gnd, dnd);
+    const TA gn = (TA)gnd, dn = (TA)dnd;
     ++it;
-    if (gn <= stop) break;
+    if (gnd <= stop) break;
     beta = div3(gn, gamma);
     const TA den = dn - beta * div3(gn, alpha);
     if (!(den > TA(0))) {
@@ -1176,12 +1176,27 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       }
       tangent3<TA, false>(c, w, nullptr);
       // The coarse levels are built on the first Newton iteration of a solve (or continuation
-      // stage) and reused by the later ones: a V-cycle with coarse operators of a nearby tangent,
-      // current fine smoothing and current fine residuals is still symmetric positive definite,
-      // only slightly less effective.  The tangent transfer rebuilds them at the converged state.
+      // stage) and reused by the later ones, with the current fine operator, smoother and
+      // residual.  The V-cycle stays symmetric; it stays positive definite as long as the reused
+      // Galerkin operators are positive definite and the damped smoother still contracts at the
+      // current tangent, which holds for nearby tangents but is not guaranteed under large
+      // stretch and stiffness contrast.  So a PCG that breaks down or hits its cap with reused
+      // levels is run again once with levels rebuilt at the current tangent (its right-hand side
+      // is kept in the transfer area, unused during Newton).  The tangent transfer always
+      // rebuilds them at the converged state.
+      const bool reused = c.mg.levels && it > 0;
       if (c.mg.levels && it == 0) mg3_build<TA>(c);
+      if (reused)
+        for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.L[v] = c.sc.r[v];
       int pst = kStatusOk;
       cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
+      if (reused && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap)) {
+        mg3_build<TA>(c);
+        for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.r[v] = c.sc.L[v];
+        __syncthreads();
+        pst = kStatusOk;
+        cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
+      }
       if (pst == kStatusPcgBreakdown) {
         status = kStatusPcgBreakdown;
         break;

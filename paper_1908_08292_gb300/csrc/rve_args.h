@@ -69,7 +69,7 @@ struct MacroSolveArgs {
   const double* f;          // macro residual
   const uint8_t* fixed;     // [n] 1 = Dirichlet dof
   double* du;               // [n] correction (output)
-  double* work;             // 6n + 2*blocks doubles
+  double* work;             // 6n + 4*blocks doubles (two alternating partial-sum buffers)
   double* out;              // [3]: |f_free|_2, iterations, status (0 ok, 1 cap, 2 breakdown)
   double rtol;
   int max_it;

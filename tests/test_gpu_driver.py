@@ -51,12 +51,53 @@ def test_macro_solve_matches_direct_solve(n_el):
     assert np.all(du[dofs] == 0)
 
 
+def test_macro_solve_repeatable_with_one_block_per_sm():
+    """The cooperative macro CG with the largest grid (one block per SM) run many times on the same
+    system: every run must give a bit-identical correction and the same iteration count.  Each
+    block adds the grid's partial sums itself, so a block that read another call's partials (the
+    reuse of one partial buffer by back-to-back grid reductions) would take different step
+    lengths from the others; the reductions alternate between two buffers to exclude that."""
+    import torch
+
+    import paper_1908_08292_gb300 as fe
+
+    n_el = (52, 48)  # 5194 rows: more rows than 32 x (number of SMs), so one block per SM
+    mesh = MacroMesh(n_el)
+    lam, mu = mat.lame(3.0, 0.3)
+    F = synth.random_F(502, mesh.n_qp, 2, 0.05)
+    P, A = mat.P_of_F(F, lam, mu), mat.A_of_F(F, lam, mu)
+    fixed = np.nonzero(np.isclose(mesh.X[:, 0], 0.0))[0]
+    dofs = np.concatenate([2 * fixed, 2 * fixed + 1]).astype(np.int32)
+    dev = torch.device("cuda:0")
+    assert torch.cuda.get_device_properties(dev).multi_processor_count * 32 < mesh.n_dof
+    with fe.Context(2, "fp64") as ctx:
+        ctx.macro_create(n_el)
+        ctx.macro_set_dirichlet(dofs, np.zeros(dofs.size))
+        _, _, nr, nnz = ctx.macro_csr()
+        f = torch.zeros(nr, dtype=torch.float64, device=dev)
+        K = torch.zeros(nnz, dtype=torch.float64, device=dev)
+        ctx.macro_assemble(torch.tensor(P.reshape(-1, 4), device=dev), torch.tensor(A.reshape(-1, 16), device=dev),
+                           f, K)
+        runs = 40
+        du = torch.zeros(runs, nr, dtype=torch.float64, device=dev)
+        info = torch.zeros(runs, 3, dtype=torch.float64, device=dev)
+        for k in range(runs):
+            ctx.macro_solve(K, f, du[k], info[k], rtol=1e-12, max_it=20000)
+        torch.cuda.synchronize()
+        du, info = du.cpu().numpy(), info.cpu().numpy()
+    assert np.all(info[:, 2] == 0)
+    assert np.all(info[:, 1] == info[0, 1]) and info[0, 1] > 10
+    assert np.array_equal(du, np.broadcast_to(du[0], du.shape))
+
+
 @pytest.mark.parametrize("scheme", ["nested", "alternating"])
 def test_config1_load_steps_match_oracle(scheme):
+    """All ten load steps of config 1 (uniaxial stretch to 10 %) against the oracle's Algorithm 1
+    or 2."""
     from paper_1908_08292_gb300.driver import LoadStepDriver
 
     p = synth.config1()
-    steps = 3
+    steps = 10
     ref, mesh = odriver.run(p, scheme=scheme, steps_to_run=steps, micro_rtol=1e-12)
     drv = LoadStepDriver(p, precision="fp64", scheme=scheme, newton_rtol=1e-12, newton_atol=1e-15, cg_rtol=1e-9,
                          cond_rtol=1e-11)

@@ -66,6 +66,23 @@ def test_noalloc_matches_context_entry_point_on_two_calls():
             assert rel_err(P[q], ref["P"][q], 1e-3) < 1e-10
             assert rel_err(A[q], ref["A"][q], 1e-3) < 1e-10
             assert np.abs(w[q] - ref["w"][q]).max() < 1e-10
+    # a device phase map with an id outside the 4-entry material table: that point is reported
+    # with FEHMM_RVE_BAD_PHASE (7) before any table read and left unsolved; the others solve
+    bad = np.stack([phase, phase])
+    bad[1, 5] = 6
+    bad_d = torch.tensor(bad, dtype=torch.uint8, device=dev)
+    table2 = torch.tensor(np.stack([table, table]).reshape(-1), dtype=torch.float64, device=dev)
+    Fs = synth.random_F(403, 2, 2, 0.05)
+    F = torch.tensor(Fs.reshape(2, 4), dtype=torch.float64, device=dev)
+    w = torch.zeros(2 * n * n * 2, dtype=torch.float64, device=dev)
+    P = torch.full((2, 4), 7.0, dtype=torch.float64, device=dev)
+    st = torch.full((2,), -1, dtype=torch.int32, device=dev)
+    rc = L.fehmm_rve2d_solve_fp64_noalloc(2, n, 1, _ptr(bad_d), _ptr(table2), _ptr(w), _ptr(F), _ptr(P), None,
+                                           _ptr(st), None, ctypes.byref(opt), stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    st, P = st.cpu().numpy(), P.cpu().numpy()
+    assert st[0] == 0 and st[1] == 7 and np.all(P[1] == 7.0)
     # a grid beyond the static scratch is rejected before any launch
     rc = L.fehmm_rve2d_solve_fp64_noalloc(1, 18, 0, _ptr(phase_d), _ptr(table_d), _ptr(table_d), _ptr(table_d),
                                            _ptr(table_d), None, _ptr(table_d), None, ctypes.byref(opt), stream)
