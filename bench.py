@@ -1,18 +1,22 @@
 """Benchmark of the batched periodic-RVE hot path on one (or N) GB300.
 
-Workload (one "step"): the 2D plane-strain FE-HMM workload with a 32x32 Q1 macro mesh
-(4096 macro quadrature points) and one 32x32 Q1 periodic RVE per point (random circular
-inclusion, stiffness ratio 5-50), mixed FP32/FP64 precision.  A step is one macro iteration
-of the hot path: Fbar at the quadrature points from the macro displacement, the batched RVE
-Newton solves with homogenised stress and tangent (starting from the committed fluctuations
-of the previous load step), the macro residual/tangent assembly and the macro Newton
-correction (GPU CG on the assembled tangent).
+Workload: the 2D plane-strain FE-HMM workload with a 32x32 Q1 macro mesh (4096 macro quadrature
+points) and one 32x32 Q1 periodic RVE per point (random circular inclusion, stiffness ratio
+5-50), mixed FP32/FP64 precision, loaded to biaxial 30% + shear 0.3 in 20 steps.  One timed
+"step" is one whole load step of the nested scheme: macro iterations to macro convergence, each
+Fbar at the quadrature points -> the batched RVE Newton solves with homogenised stress and
+tangent -> macro residual/tangent assembly -> macro CG correction, starting from the converged
+state of the previous load step.  The K timed steps cycle through load steps 1, 10 and 20 (the
+states are reached by running the whole load path once before timing; it is reported too).
 
-Value: RVE solves per second (whole job, all ranks).  Also reported: micro-DOF x Newton
-iterations per second.  `--impl reference` times the FP64 CPU oracle on a bounded sample
-of the same workload instead.
+Value: RVE solves per second (whole job, all ranks).  Also reported: per-load-step rates,
+micro-DOF x Newton iterations per second, the RVE kernel's ALU roofline fraction, parity of
+P and A against the FP64 oracle at the GPU's own Fbar, and the oracle's rate on one and on all
+host cores.  `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.  `--mode iteration` times macro iteration 1 of one load step from the zero
+state (the short form used for profiling).
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--step-index S]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload c2|c3|...]
 """
 from __future__ import annotations
 
@@ -62,6 +66,13 @@ FP32_FLOP_PER_ELEMENT_MG_ITER_3D = 8400.0
 FP32_FLOP_PER_ELEMENT_MG_BUILD_3D = 29000.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
+
+
+# DRAM bytes per RVE solve of the dominant kernel from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch / RVEs in that launch), with the profile summary it comes
+# from; scaled to a launch of the bench by the RVEs it solves.  Empty until the current kernel
+# has been captured.
+TRAFFIC_PER_LAUNCH = {}
 
 
 def workload_config(step_index):
@@ -207,7 +218,344 @@ def flops_2d(n, iters, mg=False):
     return f64, f32
 
 
+TIMED_LOAD_STEPS = {"c2": (1, 10, 20), "c3": (1, 5, 10)}
+
+
+def measured_peaks(dev):
+    """cuBLAS DGEMM and SGEMM (TF32 off) rates on this GPU, measured live: the FP64 denominator of
+    the ALU roofline and a cross-check of the FP32 unit-count peak."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n in (("fp64_dgemm_tflops", torch.float64, 4096), ("fp32_sgemm_tflops", torch.float32, 8192)):
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            for _ in range(2):
+                torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = 1e30
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    out["how"] = "torch.matmul (cuBLAS) float64 4096^3 and float32 8192^3 with TF32 off, best of 5, CUDA events"
+    return out
+
+
+def _oracle_rve(task):
+    """One FP64 oracle RVE solve (module-level so that a spawned pool can run it)."""
+    n, dim, phase, E, nu, F, rtol = task
+    from oracle.rve import PeriodicRVE
+    r = PeriodicRVE(n, dim, phase, E, nu).solve(F, rtol=rtol)
+    return r["P"], r["A"]
+
+
+def oracle_parity_and_baseline(p, F, P, A, qps, budget_s, label):
+    """The FP64 oracle on one host core at the GPU's own Fbar of the given points (first ones, until
+    the time budget is spent): per-point relative error of the GPU's P and A against it, and the
+    oracle's rate.  Returns (parity dict, seconds, solves)."""
+    d = p.dim
+    t0 = time.perf_counter()
+    eP, eA, done = [], [], 0
+    for q in qps:
+        if time.perf_counter() - t0 > budget_s and done >= 4:
+            break
+        r = p.qp_rve[q]
+        Pr, Ar = _oracle_rve((int(p.rve_n[r]), d, p.rve_phase[r], p.rve_E[r], p.rve_nu[r], F[q].reshape(d, d),
+                              1e-12))
+        eP.append(np.linalg.norm(P[q] - Pr.reshape(-1)) / max(np.linalg.norm(Pr), 1e-3))
+        eA.append(np.linalg.norm(A[q] - Ar.reshape(-1)) / np.linalg.norm(Ar))
+        done += 1
+    dt = time.perf_counter() - t0
+    return ({"state": label, "n": done, "max_rel_P": float(max(eP)), "max_rel_A": float(max(eA)),
+             "tolerance": 1e-5}, dt, done)
+
+
+def cpu_all_cores(p, F, qps, budget_s):
+    """The oracle over a spawned process pool on every host core (one solve per task, BLAS
+    threads pinned to 1): RVE solves/s on a bounded sample of the same points."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    d = p.dim
+    tasks = []
+    for q in qps:
+        r = p.qp_rve[q]
+        tasks.append((int(p.rve_n[r]), d, p.rve_phase[r], p.rve_E[r], p.rve_nu[r], F[q].reshape(d, d), 1e-10))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_rve, tasks[:cores])  # start-up (imports) outside the timed part
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < budget_s and n < len(tasks):
+            m = min(len(tasks) - n, cores * 2)
+            pool.map(_oracle_rve, tasks[n:n + m])
+            n += m
+        dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} RVE solves (points of the bench's load-step-1 state, the GPU's own Fbar), "
+                      f"{dt:.1f} s over a spawned pool of {cores} processes"}
+
+
 def run_gpu(args):
+    """Default mode: whole load steps of the load path.  A timed step is one complete load step
+    (every macro iteration to macro convergence: Fbar, the batched RVE solves, assembly, macro
+    CG, and the final accuracy pass) started from the converged state of the previous step; the
+    K timed steps cycle through load steps TIMED_LOAD_STEPS (e.g. 1, 10 and 20 of 20).  The
+    states are reached by running the load path once before timing."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1908_08292_gb300 as fe
+    from paper_1908_08292_gb300.driver import LoadStepDriver
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    wl = _SIZE["workload"]
+    _SIZE["world"] = world if wl == "c2" else 1
+    fe.lib()
+    p, _ = build_problem(1)
+    d = p.dim
+    opts = {k: v for k, v in (("cg_rtol", args.cg_rtol), ("cond_rtol", args.cond_rtol)) if v is not None}
+    opts["precond"] = fe.PRECOND_MG if args.precond == "mg" else fe.PRECOND_JACOBI
+    shard = None
+    if _SIZE["world"] > 1:
+        from paper_1908_08292_gb300.dist import Shard
+        dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve])
+        shard = Shard.make(rank, world, dofs, 2 ** d)
+    drv = LoadStepDriver(p, precision="mixed", shard=shard, **opts)
+    ctx = drv.ctx
+    steps_timed = TIMED_LOAD_STEPS[wl]
+    n_total = p.n_qp if _SIZE["world"] > 1 else p.n_qp * world  # sharded mesh, or replicas
+    mine = shard.qps if shard is not None else np.arange(p.n_qp)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks(dev)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # ---- the load path once (set-up, also reported); snapshots of the states the timed steps start from
+    snaps, path = {}, []
+    for k in range(1, max(steps_timed) + 1):
+        if k in steps_timed:
+            snaps[k] = (drv.u.clone(), ctx.fluctuations(committed=True).clone())
+        e0, e1 = ev()
+        e0.record(stream)
+        rec = drv.load_step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        path.append({"step": k, "ms": e0.elapsed_time(e1), "rve_passes": rec["rve_passes"],
+                     "macro_iters": rec["macro_iters"], "converged": rec["converged"]})
+
+    def restore(k):
+        u0, w0 = snaps[k]
+        drv.u.copy_(u0)
+        ctx.fluctuations(committed=True).copy_(w0)
+        ctx.rollback()
+        flush.zero_()
+
+    for j in range(args.warmup):
+        restore(steps_timed[j % len(steps_timed)])
+        drv.load_step(steps_timed[j % len(steps_timed)], commit=False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launches
+    recs = []
+    with ClockSampler(local) as clk:
+        for j in range(args.steps):
+            k = steps_timed[j % len(steps_timed)]
+            restore(k)
+            drv.rve_events = []
+            e0, e1 = ev()
+            e0.record(stream)
+            rec = drv.load_step(k, commit=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            recs.append({"k": k, "ms": e0.elapsed_time(e1), "passes": rec["rve_passes"],
+                         "rve_ms": [a.elapsed_time(b) for a, b in drv.rve_events],
+                         "macro_iters": rec["macro_iters"], "converged": rec["converged"]})
+            drv.rve_events = None
+    launches = ctx.launches - launches0
+    if world > 1:
+        dist.barrier()
+    t_total = sum(r["ms"] for r in recs) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    solves = sum(r["passes"] for r in recs) * n_total
+
+    # ---- operation counts (untimed repetition of each timed load step; the 2D solves are
+    # deterministic per point, the 3D ones up to the order of float atomics)
+    counts = {}
+    for k in steps_timed:
+        restore(k)
+        drv.iter_log = []
+        drv.load_step(k, commit=False)
+        its = [t.cpu().numpy()[mine] for t in drv.iter_log]
+        drv.iter_log = None
+        f64 = f32 = 0.0
+        newton = cg = tr = 0.0
+        for it in its:
+            a, b = (flops_2d(RVE_N, it, args.precond == "mg") if d == 2 else flops_3d(p, it, args.precond == "mg"))
+            f64 += a
+            f32 += b
+            newton += float(it[:, 0].mean())
+            cg += float(it[:, 1].mean())
+            tr += float(it[:, 2].mean())
+        counts[k] = {"f64": f64, "f32": f32, "passes": len(its), "newton_per_rve_pass": newton / len(its),
+                     "pcg_per_rve_pass": cg / len(its), "transfer_pcg_per_rve_pass": tr / len(its)}
+
+    # ---- parity with the FP64 oracle at the GPU's own Fbar (final pass of load steps 1 and last)
+    parity, cpu_one = [], None
+    for k in (steps_timed[0], steps_timed[-1]):
+        restore(k)
+        drv.load_step(k, commit=False)
+        torch.cuda.synchronize()
+        Fh, Ph, Ah = drv.F.cpu().numpy(), drv.P.cpu().numpy(), drv.A.cpu().numpy()
+        if rank == 0 and not args.no_cpu_baseline:
+            budget = args.cpu_seconds if k == steps_timed[0] else args.cpu_seconds / 3
+            par, dt, n = oracle_parity_and_baseline(p, Fh, Ph, Ah, mine, budget, f"load step {k}, final pass")
+            parity.append(par)
+            if k == steps_timed[0]:
+                cpu_one = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                           "sample": f"first {n} of {p.n_qp} points at the GPU's Fbar of load step {k} (final "
+                                     f"pass), full Newton + tangent transfer, scipy sparse LU, {dt:.1f} s on one "
+                                     f"host core"}
+                F_state1 = Fh
+
+    # ---- end to end through the public API with host buffers (H2D of u, D2H of u, P, A, status)
+    u_h = torch.empty_like(drv.u, device="cpu").pin_memory()
+    outs_h = [torch.empty_like(t, device="cpu").pin_memory() for t in (drv.u, drv.P, drv.A, drv.st)]
+    e2e_s, e2e_solves = 0.0, 0
+    for j in range(max(1, args.steps)):
+        k = steps_timed[j % len(steps_timed)]
+        restore(k)
+        u_h.copy_(snaps[k][0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        drv.u.copy_(u_h, non_blocking=True)
+        rec = drv.load_step(k, commit=False)
+        for h, t in zip(outs_h, (drv.u, drv.P, drv.A, drv.st)):
+            h.copy_(t, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        e2e_solves += rec["rve_passes"] * n_total
+    h2d = u_h.numel() * 8
+    d2h = sum(h.numel() * h.element_size() for h in outs_h)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    value = solves / t_total
+    per_step = {}
+    for k in steps_timed:
+        rs = [r for r in recs if r["k"] == k]
+        if rs:
+            t = sum(r["ms"] for r in rs) / 1e3
+            per_step[str(k)] = {"rve_solves_per_s": sum(r["passes"] for r in rs) * n_total / t,
+                                "ms_per_load_step": 1e3 * t / len(rs), "macro_iters": rs[0]["macro_iters"],
+                                "rve_passes": rs[0]["passes"], **{kk: v for kk, v in counts[k].items()
+                                                                  if kk not in ("f64", "f32", "passes")}}
+    # dominant kernel: the batched RVE solve; achieved = algorithmic flops per launch / mean launch time
+    rve_ms = [m for r in recs for m in r["rve_ms"]]
+    n_launch = len(rve_ms)
+    f64 = sum(counts[r["k"]]["f64"] for r in recs)
+    f32 = sum(counts[r["k"]]["f32"] for r in recs)
+    t_launch = statistics.mean(rve_ms) / 1e3
+    fp64_peak = peaks["fp64_dgemm_tflops"]
+    ach_eq = (f32 + f64 * FP32_PEAK_TFLOPS / fp64_peak) / n_launch / t_launch / 1e12
+    dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve[mine]], dtype=np.float64)
+    dof_iter = sum(counts[r["k"]]["newton_per_rve_pass"] * counts[r["k"]]["passes"] for r in recs) \
+        * float(dofs.mean()) * n_total / t_total
+    traffic = TRAFFIC_PER_LAUNCH.get((wl, args.precond))
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed: FP64 residual/sums, FP32 tangent/PCG)",
+        "data": "synthetic (seeded generator, config shapes)", "config": path_config(steps_timed),
+        "micro_dof_newton_iter_per_s": dof_iter,
+        "rve_preconditioner": ("multigrid V(1,1) with Galerkin coarse levels" if args.precond == "mg"
+                               else "block-Jacobi"),
+        "timed_steps_converged": all(r["converged"] for r in recs),
+        "per_load_step": per_step,
+        "load_path": {"steps": len(path), "seconds": sum(x["ms"] for x in path) / 1e3,
+                      "rve_solves": sum(x["rve_passes"] for x in path) * n_total,
+                      "rve_solves_per_s": sum(x["rve_passes"] for x in path) * n_total / (sum(x["ms"] for x in path) / 1e3),
+                      "macro_iters_per_step": [x["macro_iters"] for x in path],
+                      "all_converged": all(x["converged"] for x in path),
+                      "note": "the whole load path once, before timing (includes first-use costs)"},
+        "roofline": {"kernel": f"rve{d}d_kernel<float>", "bound": "alu",
+                     "achieved": ach_eq, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s (FP32-equivalent)",
+                     "frac": ach_eq / FP32_PEAK_TFLOPS,
+                     "traffic": traffic[0] * (n_total / world) if traffic else None,
+                     "traffic_source": traffic[1] if traffic else None,
+                     "launches": n_launch, "mean_launch_ms": t_launch * 1e3,
+                     "fp64_tflops": f64 / n_launch / t_launch / 1e12, "fp32_tflops": f32 / n_launch / t_launch / 1e12,
+                     "note": "FP32 peak from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz); FP64 flops weighted "
+                             "by FP32 peak / measured DGEMM rate; flops counted from the kernel source per unit "
+                             "x the per-point iteration counts of each launch"},
+        "peaks_measured": peaks,
+        "parity": parity,
+        "e2e": {"value": e2e_solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_one
+        out["cpu_baseline_all_cores"] = cpu_all_cores(p, F_state1, mine[: 64 * (os.cpu_count() or 1)],
+                                                      args.cpu_seconds / 2)
+    drv.close()
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def path_config(steps_timed):
+    wl = _SIZE["workload"]
+    W = _SIZE["world"]
+    MACRO = _SIZE["macro"]
+    ks = ", ".join(str(k) for k in steps_timed)
+    if wl == "c3":
+        return {"workload": f"3D FE-HMM macro {MACRO}^3 Hex8 ({MACRO ** 3 * 8} qps), one periodic Hex8 RVE per qp "
+                            f"of 8^3/12^3/16^3 elements (uniform draw), 1-4 spheres (volume fraction 0.1-0.3, "
+                            f"stiffness ratio 10), neo-Hookean, mixed FP32/FP64, uneven batch in one persistent "
+                            f"launch; a step = one whole load step (all macro iterations, nested scheme) of the "
+                            f"10-step uniaxial path to 20%, cycling load steps {ks}",
+                "n_qp": MACRO ** 3 * 8, "rve_grid": "8/12/16 mixed", "load_steps_timed": list(steps_timed),
+                "l2": "flushed (256 MB write) between timed steps"}
+    cfg = {"workload": f"2D plane-strain FE-HMM macro {MACRO}x{MACRO * W} Q1 ({MACRO * MACRO * W * 4} qps), "
+                       f"one {RVE_N}x{RVE_N} Q1 periodic RVE per qp (random circular inclusion r~U(0.15,0.35), "
+                       f"E ratio log-U[5,50]), neo-Hookean, mixed FP32/FP64; a step = one whole load step (all "
+                       f"macro iterations to convergence, nested scheme, from the previous step's converged "
+                       f"state) of the 20-step path to biaxial 30% + shear 0.3, cycling load steps {ks}",
+           "n_qp": MACRO * MACRO * W * 4, "rve_grid": RVE_N, "micro_dofs_per_rve": 2 * RVE_N * RVE_N,
+           "load_steps_timed": list(steps_timed), "l2": "flushed (256 MB write) between timed steps"}
+    if W > 1:
+        cfg["parallelism"] = (f"dp{W}: macro elements in {W} contiguous blocks balanced by RVE dofs, one per rank; "
+                              "all-reduce of f and K, macro solve on rank 0, broadcast of du")
+    return cfg
+
+
+def run_gpu_iteration(args):
+    """--mode iteration: macro iteration 1 of load step --step-index from the committed (zero)
+    state with an affine macro field, repeated (profiling runs use this short form)."""
     import torch
     import torch.distributed as dist
 
@@ -402,18 +750,24 @@ def cpu_baseline(budget_s, step_index=1):
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands on one host core, on the arm's workload: each step solves
+    --ref-rves-per-step points at the affine Fbar of the load steps the GPU arm times (cycling),
+    from zero fluctuations (bounded sample; the oracle has no batch or load-path state)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from oracle.rve import PeriodicRVE
-    p, Fload = build_problem(args.step_index)
+    p, _ = build_problem(1)
+    steps_timed = TIMED_LOAD_STEPS.get(_SIZE["workload"], (args.step_index,)) if args.mode == "path" else (args.step_index,)
     per_step = max(1, args.ref_rves_per_step)
+    F_of = {ls: build_problem(ls)[1] for ls in steps_timed}
 
     def step(k):
+        F = F_of[steps_timed[k % len(steps_timed)]]
         for j in range(per_step):
             q = (k * per_step + j) % p.n_qp
             r = p.qp_rve[q]
-            PeriodicRVE(int(p.rve_n[r]), p.dim, p.rve_phase[r], p.rve_E[r], p.rve_nu[r]).solve(Fload, rtol=1e-10)
+            PeriodicRVE(int(p.rve_n[r]), p.dim, p.rve_phase[r], p.rve_E[r], p.rve_nu[r]).solve(F, rtol=1e-10)
 
     for k in range(args.warmup):
         step(k)
@@ -422,13 +776,15 @@ def run_reference(args):
         step(args.warmup + k)
     dt = time.perf_counter() - t0
     value = per_step * args.steps / dt
+    cfg = path_config(steps_timed) if args.mode == "path" else workload_config(args.step_index)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded generator, config-2 shapes)", "config": workload_config(args.step_index),
+        "data": "synthetic (seeded generator, config shapes)", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} RVE solves of the workload per step (of {p.n_qp})"},
+                         "sample": f"{per_step} RVE solves per step at the affine Fbar of load steps "
+                                   f"{list(steps_timed)} (cycling), from zero fluctuations (of {p.n_qp} points)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -649,6 +1005,9 @@ def main():
     ap.add_argument("--cg-rtol", type=float, default=None, help="override the Newton-correction PCG tolerance")
     ap.add_argument("--cond-rtol", type=float, default=None, help="override the tangent-transfer PCG tolerance")
     ap.add_argument("--macro", type=int, default=None, help="macro elements per axis (profiling runs use less)")
+    ap.add_argument("--mode", default="path", choices=["path", "iteration"],
+                    help="path: whole load steps 1/10/20 of the load path (default); iteration: macro iteration 1 "
+                         "of --step-index from the zero state (short runs for profiling)")
     ap.add_argument("--precond", default="mg", choices=["mg", "jacobi"],
                     help="RVE PCG preconditioner: multigrid V-cycle (default; 2D) or block-Jacobi")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "schemes"],
@@ -676,6 +1035,8 @@ def main():
         _SIZE["macro"] = args.macro if args.macro is not None else 8
         args.macro = _SIZE["macro"]
         run_c5(args)
+    elif args.mode == "iteration":
+        run_gpu_iteration(args)
     else:
         run_gpu(args)
 

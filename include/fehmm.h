@@ -183,6 +183,12 @@ int fehmm_rollback(fehmm_ctx* ctx, void* stream);
  */
 int fehmm_fluctuation(fehmm_ctx* ctx, int q, int which, double** dev_ptr, int* n_values);
 
+/* The fluctuations of all bound points as one device array (the per-point fields of
+ * fehmm_fluctuation concatenated in point order; owned by the context, valid until the next
+ * bind): which = 0 current, 1 committed.  Lets a caller save and restore the load-step state
+ * of Sec. 5.1 (e.g. to repeat a load step from the same converged state). */
+int fehmm_fluctuation_all(fehmm_ctx* ctx, int which, double** dev_ptr, long long* n_values);
+
 /*
  * Structured macro mesh on [0,1]^dim with n_el[c] elements along axis c (host array of
  * dim ints).  Builds the CSR pattern of the macro tangent and the colouring of the

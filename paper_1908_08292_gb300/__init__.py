@@ -53,6 +53,7 @@ _SIGS = {
     "fehmm_commit": (_I, [_P, _P]),
     "fehmm_rollback": (_I, [_P, _P]),
     "fehmm_fluctuation": (_I, [_P, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_I)]),
+    "fehmm_fluctuation_all": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_longlong)]),
     "fehmm_macro_create": (_I, [_P, _P]),
     "fehmm_macro_qp_F": (_I, [_P, _P, _P, _P]),
     "fehmm_macro_assemble": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -246,6 +247,14 @@ class Context:
         ptr, n = _P(), _I()
         _check(lib().fehmm_fluctuation(self._h, int(q), int(committed), ctypes.byref(ptr), ctypes.byref(n)),
                "fluctuation")
+        return torch.as_tensor(_DevArray(ptr.value, n.value, "<f8"), device="cuda")
+
+    def fluctuations(self, committed: bool = False):
+        """Device view (torch float64, no copy) of every point's fluctuation, concatenated."""
+        import torch
+        ptr, n = _P(), ctypes.c_longlong()
+        _check(lib().fehmm_fluctuation_all(self._h, int(committed), ctypes.byref(ptr), ctypes.byref(n)),
+               "fluctuation_all")
         return torch.as_tensor(_DevArray(ptr.value, n.value, "<f8"), device="cuda")
 
     # ------------------------------------------------------------------ macro

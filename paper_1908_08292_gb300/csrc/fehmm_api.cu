@@ -362,6 +362,13 @@ int fehmm_fluctuation(fehmm_ctx* c, int q, int which, double** dev_ptr, int* n_v
   return FEHMM_OK;
 }
 
+int fehmm_fluctuation_all(fehmm_ctx* c, int which, double** dev_ptr, long long* n_values) {
+  if (!c || !dev_ptr || (which != 0 && which != 1) || c->n_qp <= 0) return FEHMM_ERR_ARG;
+  *dev_ptr = which ? c->d_w_comm : c->d_w_cur;
+  if (n_values) *n_values = (long long)c->w_total;
+  return FEHMM_OK;
+}
+
 int fehmm_macro_create(fehmm_ctx* c, const int32_t* n_el) {
   if (!c || !n_el) return FEHMM_ERR_ARG;
   const int d = c->opt.dim;

@@ -30,7 +30,7 @@ from . import SOLVE_FROM_COMMITTED, Context, FehmmError
 
 class LoadStepDriver:
     def __init__(self, problem, precision=None, scheme="nested", graphs=False, macro_rtol=1e-10, macro_atol=1e-13,
-                 max_macro=40, solve_rtol=1e-12, **options):
+                 max_macro=40, solve_rtol=1e-12, shard=None, **options):
         import torch
 
         if scheme not in ("nested", "alternating"):
@@ -64,28 +64,60 @@ class LoadStepDriver:
         self.f = torch.zeros(n_rows, dtype=f64, device=dev)
         self.K = torch.zeros(nnz, dtype=f64, device=dev)
         self.info = torch.zeros(3, dtype=f64, device=dev)
+        # data-parallel ranks (dist.Shard): this rank solves only its points' RVEs, the partial
+        # macro systems are summed over ranks, rank 0 solves and broadcasts du and the CG info
+        self.shard = shard
+        if shard is not None:
+            self.lst = torch.tensor(shard.qps, dtype=i32, device=dev)
+            self.cnt = torch.tensor([shard.n_local], dtype=i32, device=dev)
         self.scale = 0.0
         self.graphs = graphs
         self._g = {}
         self._warm = set()
+        # optional instrumentation: when a list, every batched RVE solve is bracketed by a pair of
+        # CUDA timing events on the current stream, appended here (eager runs only)
+        self.rve_events = None
+        # optional instrumentation: when a list, the per-point iteration counts of every batched
+        # RVE solve are copied here (for operation counts; not used by the iteration itself)
+        self.iter_log = None
 
     # ------------------------------------------------------------ one iteration
     def _constitutive(self, first):
         """Pbar, Abar at every macro point: one batched RVE solve (overridden by the surrogate path)."""
-        self.ctx.rve_solve(self.F, self.P, self.A, self.st, self.it, flags=SOLVE_FROM_COMMITTED if first else 0)
+        flags = SOLVE_FROM_COMMITTED if first else 0
+        if self.shard is None:
+            self.ctx.rve_solve(self.F, self.P, self.A, self.st, self.it, flags=flags)
+        else:
+            self.ctx.rve_solve_list(self.F, self.P, self.A, self.st, self.it, flags, self.lst, self.cnt)
 
     def _iteration(self, first, solve=True):
+        import torch
         c = self.ctx
         c.macro_update(self.u, self.du)
         c.macro_qp_F(self.u, self.F)
-        self._constitutive(first)
+        if self.rve_events is not None:
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record()
+            self._constitutive(first)
+            ev[1].record()
+            self.rve_events.append(ev)
+        else:
+            self._constitutive(first)
+        if self.iter_log is not None:
+            self.iter_log.append(self.it.clone())
         c.macro_assemble(self.P, self.A, self.f, self.K)
+        if self.shard is not None:
+            self.shard.reduce_system(self.f, self.K)
         if solve:
-            c.macro_solve(self.K, self.f, self.du, self.info, rtol=self.solve_rtol)
+            if self.shard is None or self.shard.rank == 0:
+                c.macro_solve(self.K, self.f, self.du, self.info, rtol=self.solve_rtol)
+            if self.shard is not None:
+                self.shard.share_correction(self.du)
+                self.shard.share_correction(self.info)
 
     def _run(self, first):
         import torch
-        if not self.graphs:
+        if not self.graphs or self.rve_events is not None or self.iter_log is not None:
             self._iteration(first)
             return
         key = bool(first)
@@ -101,8 +133,10 @@ class LoadStepDriver:
         self._g[key].replay()
 
     # --------------------------------------------------------------- load step
-    def load_step(self, k):
-        """Run load step k (load factor k / n_steps); returns a record of the iterations."""
+    def load_step(self, k, commit=True):
+        """Run load step k (load factor k / n_steps); returns a record of the iterations.  With
+        commit=False the converged fluctuations stay current only (the committed state of the
+        previous step is kept, so the step can be repeated after restoring u and a rollback)."""
         import torch
         t0 = time.perf_counter()
         self.scale = k / self.p.n_steps
@@ -129,10 +163,12 @@ class LoadStepDriver:
         if self.scheme == "alternating":  # final micro iteration at the converged u (Sec. 5.2)
             self._iteration(first=False, solve=False)
             micro.append(int(self.it[:, 0].sum().item()))
-        self.ctx.commit()
+        if commit:
+            self.ctx.commit()
         torch.cuda.synchronize()
         return {"step": k, "macro_iters": len(hist) - 1, "macro_hist": hist, "macro_cg": cg_its,
-                "micro_newton": micro, "converged": converged, "seconds": time.perf_counter() - t0}
+                "micro_newton": micro, "rve_passes": len(micro), "converged": converged,
+                "seconds": time.perf_counter() - t0}
 
     def run(self, steps=None):
         steps = self.p.n_steps if steps is None else steps

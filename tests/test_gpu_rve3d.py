@@ -59,6 +59,42 @@ def test_config3_generator_rves(precision):
         assert abs(out["W"][q] - refs[q]["W"]) <= TOL[precision] * abs(refs[q]["W"])
 
 
+_REF16 = {}
+
+
+def _ref16():
+    """One 16^3 RVE of the config-3 generator (the largest grid of that workload: 12288 dofs,
+    three coarse levels 8, 4, 2) at a tension-shear Fbar, solved once by the oracle (about 100 s
+    of sparse LU) and shared by the two precisions."""
+    if not _REF16:
+        p = synth.config3(macro=1, sizes=(16,), n_rve=1)
+        F = np.eye(3) + np.array([[0.08, 0.04, 0.0], [0.02, -0.02, 0.03], [0.0, 0.01, -0.02]])
+        ref = PeriodicRVE(16, 3, p.rve_phase[0], p.rve_E[0], p.rve_nu[0]).solve(F, rtol=1e-13, atol=1e-16)
+        _REF16.update(p=p, F=F, ref=ref)
+    return _REF16
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config3_16cubed_rve(precision):
+    """The 16^3 Hex8 RVE of the config-3 workload (largest scratch and multigrid depth) against
+    the oracle: P and A per point at 1e-10 (FP64) / 1e-5 (mixed), with the 8^3 and 12^3 grids of
+    the same workload in the same launch."""
+    r16 = _ref16()
+    p = r16["p"]
+    small = synth.config3(macro=1, sizes=(8, 12), n_rve=2, seed=1013)
+    sizes = [16] + [int(n) for n in small.rve_n]
+    phases = [p.rve_phase[0]] + list(small.rve_phase)
+    E = [p.rve_E[0]] + list(small.rve_E)
+    nu = [p.rve_nu[0]] + list(small.rve_nu)
+    Fs = np.stack([r16["F"], r16["F"], r16["F"]])
+    opts = STRICT if precision == "fp64" else {}
+    out = gpu_batch(3, precision, sizes, phases, E, nu, np.arange(3), Fs, **opts)
+    refs = [r16["ref"]] + [PeriodicRVE(sizes[k], 3, phases[k], E[k], nu[k]).solve(Fs[k], rtol=1e-14, atol=1e-16)
+                           for k in (1, 2)]
+    check(out, refs, TOL[precision])
+    assert np.abs(out["w"][0] - r16["ref"]["w"]).max() < (1e-10 if precision == "fp64" else 1e-6)
+
+
 def test_homogeneous_rve_is_pointwise_law_3d():
     n = 4
     Fs = synth.random_F(603, 2, 3, 0.1)
