@@ -336,7 +336,7 @@ def run_gpu(args):
         from paper_1908_08292_gb300.dist import Shard
         dofs = np.array([d * int(p.rve_n[r]) ** d for r in p.qp_rve])
         shard = Shard.make(rank, world, dofs, 2 ** d)
-    drv = LoadStepDriver(p, precision="mixed", shard=shard, **opts)
+    drv = LoadStepDriver(p, precision="mixed", shard=shard, predictor=True, **opts)
     ctx = drv.ctx
     steps_timed = TIMED_LOAD_STEPS[wl]
     n_total = p.n_qp if _SIZE["world"] > 1 else p.n_qp * world  # sharded mesh, or replicas
@@ -352,7 +352,7 @@ def run_gpu(args):
     snaps, path = {}, []
     for k in range(1, max(steps_timed) + 1):
         if k in steps_timed:
-            snaps[k] = (drv.u.clone(), ctx.fluctuations(committed=True).clone())
+            snaps[k] = drv.state()
         e0, e1 = ev()
         e0.record(stream)
         rec = drv.load_step(k)
@@ -362,10 +362,7 @@ def run_gpu(args):
                      "macro_iters": rec["macro_iters"], "converged": rec["converged"]})
 
     def restore(k):
-        u0, w0 = snaps[k]
-        drv.u.copy_(u0)
-        ctx.fluctuations(committed=True).copy_(w0)
-        ctx.rollback()
+        drv.restore(snaps[k])
         flush.zero_()
 
     for j in range(args.warmup):
@@ -447,7 +444,7 @@ def run_gpu(args):
     for j in range(max(1, args.steps)):
         k = steps_timed[j % len(steps_timed)]
         restore(k)
-        u_h.copy_(snaps[k][0])
+        u_h.copy_(snaps[k][0])  # the macro state of the step's start, staged in pinned host memory
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         drv.u.copy_(u_h, non_blocking=True)

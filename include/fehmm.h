@@ -59,6 +59,20 @@ enum { FEHMM_PREC_FP64 = 0, FEHMM_PREC_MIXED = 1 };
 /* Preconditioner of the RVE PCG solves (fehmm_options.precond). */
 enum { FEHMM_PRECOND_BLOCK_JACOBI = 0, FEHMM_PRECOND_MULTIGRID = 1 };
 
+/* Coupling of the RVE to the macro deformation (fehmm_options.bc), Sec. 3.2: periodic
+ * fluctuations (the paper's choice; the fluctuation of node 0 is pinned), or kinematically
+ * uniform boundary conditions (KUBC: u = (Fbar - I) X on the whole cell boundary, i.e. zero
+ * fluctuation on every node of the planes x_c = 0 of the node lattice, which the periodic
+ * lattice shares with x_c = 1; the modelling error of this coupling is the boundary-layer term
+ * of Eq. ModelingError). */
+enum { FEHMM_BC_PERIODIC = 0, FEHMM_BC_KUBC = 1 };
+
+/* Constitutive law of every phase (fehmm_options.law): the compressible neo-Hookean law of the
+ * paper's Sec. 6 (Eq. NH-free-energy), or the St. Venant-Kirchhoff law (linear elasticity with
+ * geometric nonlinearity, the paper's second material case in Sec. 6): psi = lam/2 (tr E)^2 +
+ * mu E:E, S = lam tr(E) I + 2 mu E, E = (F^T F - I)/2. */
+enum { FEHMM_LAW_NEO_HOOKE = 0, FEHMM_LAW_SVK = 1 };
+
 /* Per-quadrature-point RVE status written by fehmm_rve_solve. */
 enum {
   FEHMM_RVE_OK = 0,            /* Newton converged */
@@ -108,6 +122,15 @@ typedef struct {
                            grids and FEHMM_PRECOND_BLOCK_JACOBI use block-Jacobi (inverted
                            nodal d x d blocks).  The choice changes iteration counts, not the
                            tolerances the solves meet. */
+  int bc;               /* FEHMM_BC_PERIODIC (default) or FEHMM_BC_KUBC */
+  int law;              /* FEHMM_LAW_NEO_HOOKE (default) or FEHMM_LAW_SVK */
+  double mg_omega;      /* damping of the multigrid's block-Jacobi smoother, in (0, 1); the
+                           V-cycle is a positive definite preconditioner only while omega <
+                           2 / lambda_max(D^-1 K) (about 0.86 for Q1, 0.67 for Hex8 elasticity).
+                           Default 0.7 (2D), 0.6 (3D). */
+  int mg_reuse;         /* 3D multigrid: 1 (default) builds the coarse levels at the first Newton
+                           iteration of a solve and reuses them in the later ones; 0 rebuilds
+                           them at every Newton iteration */
 } fehmm_options;
 
 /* Fill `opt` with defaults for dim (2|3) and precision. */
@@ -220,6 +243,15 @@ int fehmm_macro_set_dirichlet(fehmm_ctx* ctx, int n_fixed, const int32_t* dofs, 
  * the step) and, if du != NULL, du = 0.  u, du: device [n_rows]. */
 int fehmm_macro_apply_dirichlet(fehmm_ctx* ctx, double* u, double* du, double scale, void* stream);
 
+/* Load of a prescribed Dirichlet increment on the linearised macro problem (Eq. L(GH)):
+ * g = K d, with d = dscale * (the Dirichlet end values of fehmm_macro_set_dirichlet) on the
+ * Dirichlet dofs and zero elsewhere.  K_vals device [nnz] (CSR order of fehmm_macro_csr), g device
+ * [n_rows] (output, every row).  With the tangent of the last converged state, solving
+ * K_ff delta = -g_f (fehmm_macro_solve with f = g) gives the tangent predictor of the next load
+ * step, u <- u + d + delta, which keeps the first macro iterate of a fine macro mesh from
+ * concentrating the whole increment in the boundary elements. */
+int fehmm_macro_dirichlet_load(fehmm_ctx* ctx, const double* K_vals, double dscale, double* g, void* stream);
+
 /* Macro Newton update u += du (device [n_rows] each; du is zero on Dirichlet dofs). */
 int fehmm_macro_update(fehmm_ctx* ctx, double* u, const double* du, void* stream);
 
@@ -320,7 +352,8 @@ const char* fehmm_status_str(int code);
  *   w       device double [n_qp][grid_n*grid_n][2]: fluctuation start values in, results
  *           out (the value at node 0 is taken as zero)
  *   F, P, A, status, iters: as in fehmm_rve_solve (A may be NULL: no tangent)
- *   opt     host; dim must be 2 and precision FEHMM_PREC_FP64; tolerances and caps used
+ *   opt     host; dim must be 2 and precision FEHMM_PREC_FP64; tolerances, caps and bc used;
+ *           law must be FEHMM_LAW_NEO_HOOKE (else FEHMM_ERR_UNSUPPORTED)
  * The first call on a device looks up the device address of the static array (with that
  * device current); make that first call before any stream capture.  All calls share the
  * array and the counter, which keep the last call's contents (the counter is cleared by

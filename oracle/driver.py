@@ -10,7 +10,10 @@ ends with an RVE pass at the final macro displacement, and the alternating
 scheme adds one more micro iteration after the macro residual has converged.
 The algorithms print "while residual < tolerance"; read as "while residual >
 tolerance".  The first macro iterate of a load step is the previous converged
-displacement with the Dirichlet dofs set to their new values.
+displacement with the Dirichlet dofs set to their new values, or (predictor=True; the
+paper is silent on the start of a load step) the tangent predictor: with the tangent K
+of the last converged state, the Dirichlet increment d and the interior correction
+delta solving K_ff delta = -(K d)_f of the linearised macro problem, u + d + delta.
 """
 from __future__ import annotations
 
@@ -47,7 +50,7 @@ def rve_batch(rves, qp_rve, Fbar, w, rtol=1e-10, atol=1e-14, max_iter=30, max_st
 
 
 def run(problem, scheme="nested", n_steps=None, macro_rtol=1e-10, macro_atol=1e-13, max_macro=40,
-        micro_rtol=None, micro_atol=1e-14, steps_to_run=None, log=None):
+        micro_rtol=None, micro_atol=1e-14, steps_to_run=None, log=None, predictor=False):
     """Run the FE-HMM load steps.  Returns per-step records (u, Pbar, Abar, iteration counts)."""
     mesh = MacroMesh(problem.macro_n)
     rves = build_rves(problem)
@@ -59,8 +62,17 @@ def run(problem, scheme="nested", n_steps=None, macro_rtol=1e-10, macro_atol=1e-
     records = []
     last = n_steps if steps_to_run is None else steps_to_run
     max_steps = 1 if scheme == "alternating" else None
+    K = None
     for k in range(1, last + 1):
         lam = k / n_steps
+        if predictor:
+            if K is None:  # tangent at the start state
+                _, A0, _, _, _, _ = rve_batch(rves, problem.qp_rve, mesh.qp_F(u), w_comm, micro_rtol, micro_atol)
+                _, K = mesh.assemble(np.zeros((problem.n_qp, d, d)), A0)
+            dvec = np.zeros(mesh.n_dof)
+            dvec[problem.dirichlet_dofs] = problem.dirichlet_end / n_steps
+            delta, _ = mesh.solve_increment(K, K @ dvec, problem.dirichlet_dofs)
+            u += dvec + delta
         u[problem.dirichlet_dofs] = lam * problem.dirichlet_end
         w = [x.copy() for x in w_comm]
         hist, micro_iters = [], []
@@ -90,6 +102,7 @@ def run(problem, scheme="nested", n_steps=None, macro_rtol=1e-10, macro_atol=1e-
             P, A, W, w, status, iters = rve_batch(rves, problem.qp_rve, Fbar, w, micro_rtol, micro_atol,
                                                   max_steps=1)
             micro_iters.append(int(iters.sum()))
+            _, K = mesh.assemble(P, A)  # the tangent of the final state (the next step's predictor)
         w_comm = w
         records.append({"step": k, "u": u.copy(), "P": P, "A": A, "W": W, "macro_iters": len(hist) - 1,
                         "macro_hist": hist, "micro_iters": micro_iters, "converged": converged})

@@ -36,7 +36,9 @@ class Options(ctypes.Structure):
                 ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("max_newton", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("max_cg", ctypes.c_int),
                 ("cond_rtol", ctypes.c_double), ("max_cond_cg", ctypes.c_int),
-                ("retry_stages", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("retry_stages", ctypes.c_int), ("precond", ctypes.c_int),
+                ("bc", ctypes.c_int), ("law", ctypes.c_int), ("mg_omega", ctypes.c_double),
+                ("mg_reuse", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -60,6 +62,7 @@ _SIGS = {
     "fehmm_macro_set_dirichlet": (_I, [_P, _I, _P, _P]),
     "fehmm_macro_apply_dirichlet": (_I, [_P, _P, _P, ctypes.c_double, _P]),
     "fehmm_macro_update": (_I, [_P, _P, _P, _P]),
+    "fehmm_macro_dirichlet_load": (_I, [_P, _P, ctypes.c_double, _P, _P]),
     "fehmm_macro_solve": (_I, [_P, _P, _P, _P, _P, ctypes.c_double, _I, _P]),
     "fehmm_macro_csr": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fehmm_launch_count": (ctypes.c_longlong, [_P]),
@@ -285,6 +288,11 @@ class Context:
         import torch
         _check(lib().fehmm_macro_apply_dirichlet(self._h, _dev(u, torch.float64, "u"), _dev(du, torch.float64, "du"),
                                                  float(scale), _stream(stream)), "macro_apply_dirichlet")
+
+    def macro_dirichlet_load(self, K_vals, dscale, g, stream=None):
+        import torch
+        _check(lib().fehmm_macro_dirichlet_load(self._h, _dev(K_vals, torch.float64, "K"), float(dscale),
+                                                _dev(g, torch.float64, "g"), _stream(stream)), "macro_dirichlet_load")
 
     def macro_update(self, u, du, stream=None):
         import torch

@@ -18,8 +18,22 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfehmm.so")
-SOURCES = ["rve2d.cu", "rve2d_k_mixed_mg.cu", "rve2d_k_mixed_bj.cu", "rve2d_k_fp64_mg.cu", "rve2d_k_fp64_bj.cu",
-           "rve2d_k_fp64_fixed.cu", "rve3d.cu", "macro.cu", "macro_solve.cu", "fehmm_api.cu", "noalloc.cu", "mlp.cu",
+SOURCES = ["rve2d.cu",
+           "rve2d_k_mixed_mg_nh.cu",
+           "rve2d_k_mixed_mg_svk.cu",
+           "rve2d_k_mixed_bj_nh.cu",
+           "rve2d_k_mixed_bj_svk.cu",
+           "rve2d_k_fp64_mg_nh.cu",
+           "rve2d_k_fp64_mg_svk.cu",
+           "rve2d_k_fp64_bj_nh.cu",
+           "rve2d_k_fp64_bj_svk.cu",
+           "rve2d_k_fp64_fixed_nh.cu",
+           "rve3d.cu",
+           "macro.cu",
+           "macro_solve.cu",
+           "fehmm_api.cu",
+           "noalloc.cu",
+           "mlp.cu",
            "surrogate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

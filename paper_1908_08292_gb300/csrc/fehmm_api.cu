@@ -49,6 +49,7 @@ struct fehmm_ctx {
   uint8_t* d_fixed = nullptr;   // Dirichlet mask of the macro dofs
   int32_t* d_fixed_dofs = nullptr;
   double* d_fixed_vals = nullptr;
+  double* d_dir_full = nullptr;  // [macro_rows]: the Dirichlet end values on their dofs, 0 elsewhere
   int n_fixed = 0;
   double* d_solve_work = nullptr;
   long long launches = 0;
@@ -79,7 +80,10 @@ bool valid_options(const fehmm_options* o) {
   return o && (o->dim == 2 || o->dim == 3) && (o->precision == FEHMM_PREC_FP64 || o->precision == FEHMM_PREC_MIXED) &&
          o->newton_rtol >= 0 && o->newton_atol >= 0 && o->max_newton >= 0 && o->cg_rtol > 0 && o->max_cg > 0 &&
          o->cond_rtol > 0 && o->max_cond_cg > 0 && o->retry_stages >= 0 && o->retry_stages <= 64 &&
-         (o->precond == FEHMM_PRECOND_BLOCK_JACOBI || o->precond == FEHMM_PRECOND_MULTIGRID);
+         (o->precond == FEHMM_PRECOND_BLOCK_JACOBI || o->precond == FEHMM_PRECOND_MULTIGRID) &&
+         (o->bc == FEHMM_BC_PERIODIC || o->bc == FEHMM_BC_KUBC) &&
+         (o->law == FEHMM_LAW_NEO_HOOKE || o->law == FEHMM_LAW_SVK) && o->mg_omega > 0.0 && o->mg_omega < 1.0 &&
+         (o->mg_reuse == 0 || o->mg_reuse == 1);
 }
 
 }  // namespace
@@ -100,6 +104,10 @@ int fehmm_default_options(fehmm_options* opt, int dim, int precision) {
   opt->max_cond_cg = 4000;
   opt->retry_stages = 4;
   opt->precond = FEHMM_PRECOND_MULTIGRID;
+  opt->bc = FEHMM_BC_PERIODIC;
+  opt->law = FEHMM_LAW_NEO_HOOKE;
+  opt->mg_omega = dim == 2 ? 0.7 : 0.6;
+  opt->mg_reuse = 1;
   return FEHMM_OK;
 }
 
@@ -144,6 +152,7 @@ int fehmm_destroy(fehmm_ctx* c) {
   dfree(c->d_fixed);
   dfree(c->d_fixed_dofs);
   dfree(c->d_fixed_vals);
+  dfree(c->d_dir_full);
   dfree(c->d_solve_work);
   delete c;
   return FEHMM_OK;
@@ -322,6 +331,10 @@ static int rve_solve_impl(fehmm_ctx* c, const double* F, double* P, double* A, d
   a.flags = flags;
   const bool mixed = c->opt.precision == FEHMM_PREC_MIXED;
   a.mg = c->opt.precond == FEHMM_PRECOND_MULTIGRID ? 1 : 0;
+  a.bc = c->opt.bc;
+  a.law = c->opt.law;
+  a.mg_omega = (float)c->opt.mg_omega;
+  a.mg_reuse = c->opt.mg_reuse;
   a.scratch_stride = c->opt.dim == 2 ? rve2d_scratch_stride(c->nn_max, mixed) : 0;
   if (cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), s) != cudaSuccess) return FEHMM_ERR_CUDA;
   const int blocks = std::min(c->n_qp, c->num_sms);
@@ -490,13 +503,15 @@ int fehmm_macro_set_dirichlet(fehmm_ctx* c, int n_fixed, const int32_t* dofs, co
   if (!c || n_fixed < 0 || (n_fixed > 0 && (!dofs || !values))) return FEHMM_ERR_ARG;
   if (!c->has_macro) return FEHMM_ERR_STATE;
   std::vector<uint8_t> mask((size_t)c->macro_rows, 0);
+  std::vector<double> full((size_t)c->macro_rows, 0.0);
   for (int k = 0; k < n_fixed; ++k) {
     if (dofs[k] < 0 || dofs[k] >= c->macro_rows) return FEHMM_ERR_ARG;
     mask[dofs[k]] = 1;
+    full[dofs[k]] = values[k];
   }
   int rc;
   if ((rc = dupload(c->d_fixed, mask.data(), mask.size())) || (rc = dupload(c->d_fixed_dofs, dofs, (size_t)n_fixed)) ||
-      (rc = dupload(c->d_fixed_vals, values, (size_t)n_fixed)))
+      (rc = dupload(c->d_fixed_vals, values, (size_t)n_fixed)) || (rc = dupload(c->d_dir_full, full.data(), full.size())))
     return rc;
   c->n_fixed = n_fixed;
   return FEHMM_OK;
@@ -508,6 +523,25 @@ int fehmm_macro_apply_dirichlet(fehmm_ctx* c, double* u, double* du, double scal
   if (macro_dirichlet_launch(u, du, c->macro_rows, c->d_fixed_dofs, c->d_fixed_vals, c->n_fixed, scale,
                              (cudaStream_t)stream) != cudaSuccess)
     return FEHMM_ERR_CUDA;
+  c->launches += 1;
+  return FEHMM_OK;
+}
+
+int fehmm_macro_dirichlet_load(fehmm_ctx* c, const double* K_vals, double dscale, double* g, void* stream) {
+  if (!c || !K_vals || !g) return FEHMM_ERR_ARG;
+  if (!c->has_macro) return FEHMM_ERR_STATE;
+  if (!c->d_dir_full) {  // no Dirichlet data: the load is zero
+    if (cudaMemsetAsync(g, 0, sizeof(double) * (size_t)c->macro_rows, (cudaStream_t)stream) != cudaSuccess) {
+      cudaGetLastError();
+      return FEHMM_ERR_CUDA;
+    }
+    return FEHMM_OK;
+  }
+  if (macro_spmv_launch(c->d_rowptr, c->d_col, K_vals, c->d_dir_full, dscale, g, c->macro_rows,
+                        (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FEHMM_ERR_CUDA;
+  }
   c->launches += 1;
   return FEHMM_OK;
 }

@@ -166,7 +166,34 @@ __global__ void macro_update_kernel(double* u, const double* du, int n) {
   if (t < n) u[t] += du[t];
 }
 
+// y = scale K x over all rows (CSR; 8 lanes per row, 4 rows per warp, shuffle sum).  The loop
+// bound is uniform over each warp (its 4 rows share `base`), so the shuffles see all lanes.
+__global__ void macro_spmv_kernel(const int32_t* rowptr, const int32_t* col, const double* K, const double* x,
+                                  double scale, double* y, int n) {
+  const int lane8 = threadIdx.x & 7, sub = (threadIdx.x & 31) >> 3;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, warps = (gridDim.x * blockDim.x) >> 5;
+  for (int base = 4 * warp; base < n; base += 4 * warps) {
+    const int i = base + sub;
+    double s = 0.0;
+    if (i < n)
+      for (int k = rowptr[i] + lane8; k < rowptr[i + 1]; k += 8) s = fma(K[k], x[col[k]], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (lane8 == 0 && i < n) y[i] = scale * s;
+  }
+}
+
 }  // namespace
+
+cudaError_t macro_spmv_launch(const int32_t* rowptr, const int32_t* col, const double* K, const double* x,
+                              double scale, double* y, int n, cudaStream_t stream) {
+  const int threads = 256, rows_per_block = threads / 8;
+  int blocks = (n + rows_per_block - 1) / rows_per_block;
+  blocks = blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks);
+  macro_spmv_kernel<<<blocks, threads, 0, stream>>>(rowptr, col, K, x, scale, y, n);
+  return cudaGetLastError();
+}
 
 cudaError_t macro_dirichlet_launch(double* u, double* du, int n, const int32_t* dofs, const double* vals, int n_fixed,
                                    double scale, cudaStream_t stream) {

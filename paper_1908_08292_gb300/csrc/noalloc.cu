@@ -83,8 +83,10 @@ extern "C" int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_pe
   if (grid_n < 2 || (grid_n % 2) != 0) return FEHMM_ERR_ARG;
   if (grid_n * grid_n > kNoallocMaxNN) return FEHMM_ERR_TOO_LARGE;
   if (!(opt->cg_rtol > 0) || !(opt->cond_rtol > 0) || opt->max_cg <= 0 || opt->max_cond_cg <= 0 ||
-      opt->max_newton < 0 || opt->retry_stages < 0 || opt->retry_stages > 64)
+      opt->max_newton < 0 || opt->retry_stages < 0 || opt->retry_stages > 64 ||
+      (opt->bc != FEHMM_BC_PERIODIC && opt->bc != FEHMM_BC_KUBC))
     return FEHMM_ERR_ARG;
+  if (opt->law != FEHMM_LAW_NEO_HOOKE) return FEHMM_ERR_UNSUPPORTED;  // one law in the static variant
   DeviceSlots slots;
   int rc = device_slots(&slots);
   if (rc != FEHMM_OK) return rc;
@@ -115,6 +117,10 @@ extern "C" int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_pe
   a.max_cond_cg = opt->max_cond_cg;
   a.retry_stages = opt->retry_stages;
   a.mg = 0;  // block-Jacobi: the static scratch holds no multigrid levels
+  a.bc = opt->bc == FEHMM_BC_KUBC ? 1 : 0;
+  a.law = 0;
+  a.mg_omega = 0.7f;
+  a.mg_reuse = 0;
   a.scratch_stride = 72LL * a.nn_max;
   a.flags = A ? 0 : kFlagNoTangent;
   // the shared work counter keeps the previous call's value: clear it on this stream

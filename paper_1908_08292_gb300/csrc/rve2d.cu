@@ -5,11 +5,15 @@
 
 namespace fehmm {
 
-cudaError_t rve2d_launch_mixed_mg(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
-cudaError_t rve2d_launch_mixed_bj(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
-cudaError_t rve2d_launch_fp64_mg(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
-cudaError_t rve2d_launch_fp64_bj(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
-cudaError_t rve2d_launch_fp64_fixed(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_mixed_mg_nh(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_mixed_mg_svk(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_mixed_bj_nh(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_mixed_bj_svk(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_fp64_mg_nh(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_fp64_mg_svk(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_fp64_bj_nh(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_fp64_bj_svk(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
+cudaError_t rve2d_launch_fp64_fixed_nh(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream);
 
 size_t rve2d_smem_bytes(int nn_max, bool mixed) {
   return mixed ? smem2d_layout<float>(nn_max, nullptr, nullptr) : smem2d_layout<double>(nn_max, nullptr, nullptr);
@@ -25,16 +29,21 @@ size_t rve2d_scratch_bytes(int nn_max, bool mixed, int n_blocks) {
 
 int rve2d_threads() { return kThreads2D; }
 
-// The multigrid and block-Jacobi paths are separate instantiations, so each is register-
-// allocated on its own.
+// The multigrid and block-Jacobi paths and the two laws are separate instantiations, so each is
+// register-allocated on its own.
 cudaError_t rve2d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream) {
   const size_t smem = rve2d_smem_bytes(a.nn_max, mixed);
-  if (mixed) return a.mg ? rve2d_launch_mixed_mg(a, n_blocks, smem, stream) : rve2d_launch_mixed_bj(a, n_blocks, smem, stream);
-  return a.mg ? rve2d_launch_fp64_mg(a, n_blocks, smem, stream) : rve2d_launch_fp64_bj(a, n_blocks, smem, stream);
+  const bool svk = a.law == 1;
+  if (mixed) {
+    if (a.mg) return svk ? rve2d_launch_mixed_mg_svk(a, n_blocks, smem, stream) : rve2d_launch_mixed_mg_nh(a, n_blocks, smem, stream);
+    return svk ? rve2d_launch_mixed_bj_svk(a, n_blocks, smem, stream) : rve2d_launch_mixed_bj_nh(a, n_blocks, smem, stream);
+  }
+  if (a.mg) return svk ? rve2d_launch_fp64_mg_svk(a, n_blocks, smem, stream) : rve2d_launch_fp64_mg_nh(a, n_blocks, smem, stream);
+  return svk ? rve2d_launch_fp64_bj_svk(a, n_blocks, smem, stream) : rve2d_launch_fp64_bj_nh(a, n_blocks, smem, stream);
 }
 
 cudaError_t rve2d_launch_fixed_fp64(const Rve2dArgs& a, int n_blocks, cudaStream_t stream) {
-  return rve2d_launch_fp64_fixed(a, n_blocks, rve2d_smem_bytes(a.nn_max, false), stream);
+  return rve2d_launch_fp64_fixed_nh(a, n_blocks, rve2d_smem_bytes(a.nn_max, false), stream);
 }
 
 }  // namespace fehmm

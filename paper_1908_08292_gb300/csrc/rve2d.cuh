@@ -54,10 +54,10 @@ __device__ __forceinline__ double gauss01(int g) {
   return g == 0 ? 0.21132486540518711775 : 0.78867513459481288225;
 }
 
-// Multigrid level counts and region sizes (the preconditioner itself is further below).
-// Damping of the block-Jacobi smoother; the V-cycle stays positive definite for
-// omega < 2 / lambda_max(D^-1 K), about 0.86 for Q1 elasticity (lambda_max about 2.3, measured).
-constexpr float kMgOmega = 0.7f;
+// Multigrid level counts and region sizes (the preconditioner itself is further below).  The
+// damping omega of its block-Jacobi smoother is a run-time option (default 0.7); the V-cycle
+// stays positive definite for omega < 2 / lambda_max(D^-1 K), about 0.86 for Q1 elasticity
+// (lambda_max about 2.3, measured).
 constexpr int kMgMaxLevels = 4;  // coarse levels: 32 -> 16, 8, 4
 
 // Number of coarse levels (0: no multigrid for this grid).
@@ -156,15 +156,20 @@ __host__ __device__ inline size_t smem2d_layout(int NN, Smem2D<TA>* s, unsigned 
 }
 
 // Per-thread geometry of the owned node pair.
+// Pinned nodes of the fluctuation field: node 0 for periodic coupling (translation), every node
+// on the lattice lines i = 0 or j = 0 for KUBC (the cell boundary, where the fluctuation vanishes).
+__device__ __forceinline__ bool pinned2(int i, int j, int bc) { return bc ? (i == 0 || j == 0) : (i == 0 && j == 0); }
+
 struct Own2D {
   int n, NN, col, strip;
   bool active;
+  bool pin[2];   // owned nodes pinned (zero fluctuation)
   int node[2];   // (col, 2*strip), (col, 2*strip+1)
   int rows[4];   // (2s-1, 2s, 2s+1, 2s+2 periodic) * n: row offsets
   int cols[3];   // col-1, col, col+1 (periodic)
 };
 
-__device__ __forceinline__ Own2D make_own(int n) {
+__device__ __forceinline__ Own2D make_own(int n, int bc) {
   Own2D o;
   o.n = n;
   o.NN = n * n;
@@ -176,6 +181,8 @@ __device__ __forceinline__ Own2D make_own(int n) {
   const int r0 = 2 * o.strip;
   o.node[0] = o.col + n * r0;
   o.node[1] = o.node[0] + n;
+  o.pin[0] = pinned2(o.col, r0, bc);
+  o.pin[1] = pinned2(o.col, r0 + 1, bc);
   o.rows[0] = ((r0 - 1 + n) % n) * n;
   o.rows[1] = r0 * n;
   o.rows[2] = ((r0 + 1) % n) * n;
@@ -197,9 +204,37 @@ struct Stencil {
   __device__ __forceinline__ TA get(int nb, int c, int node) const { return g[(size_t)(nb * 4 + c) * NN + node]; }
 };
 
+// ------------------------------------------------------------------ constitutive laws (2D)
+// kLawNH: the paper's neo-Hookean law (factored form in fehmm_device.cuh).  kLawSVK: St.
+// Venant-Kirchhoff, S = lam tr(E) I + 2 mu E with E = (F^T F - I)/2 (plane strain: E_33 = 0).
+constexpr int kLawNH = 0, kLawSVK = 1;
+
+// First Piola-Kirchhoff stress at one point; returns J = det F.
+template <int LAW, typename T>
+__device__ __forceinline__ T law2_P(T F00, T F01, T F10, T F11, T lam, T mu, T& P00, T& P01, T& P10, T& P11) {
+  if constexpr (LAW == kLawNH) {
+    const NH2<T> q = nh2_eval(F00, F01, F10, F11, lam, mu);
+    P00 = fma(mu, F00, q.hb * q.f00);
+    P01 = fma(mu, F01, q.hb * q.f01);
+    P10 = fma(mu, F10, q.hb * q.f10);
+    P11 = fma(mu, F11, q.hb * q.f11);
+    return q.J;
+  } else {
+    const T c00 = F00 * F00 + F10 * F10, c01 = F00 * F01 + F10 * F11, c11 = F01 * F01 + F11 * F11;
+    const T trE = T(0.5) * (c00 + c11) - T(1);
+    const T S00 = lam * trE + mu * (c00 - T(1)), S11 = lam * trE + mu * (c11 - T(1)), S01 = mu * c01;
+    P00 = F00 * S00 + F01 * S01;
+    P01 = F00 * S01 + F01 * S11;
+    P10 = F10 * S00 + F11 * S01;
+    P11 = F10 * S01 + F11 * S11;
+    return F00 * F11 - F01 * F10;
+  }
+}
+
 // ------------------------------------------------------------------ residual (FP64)
 // Element e's nodal forces into stage[k][e] (k = 2*local_node + comp) and this thread's
 // contributions to sum wt P and to the J <= 0 flag.
+template <int LAW>
 __device__ __forceinline__ void element_residual(int e, int n, const double2* w, const double* Fb,
                                                  double lam, double mu, double* stage_f, double (&Psum)[4],
                                                  double& bad) {
@@ -221,10 +256,9 @@ __device__ __forceinline__ void element_residual(int e, int n, const double2* w,
       const double F10 = fma(ih, fma(t, e1.y, d10.y), Fb[2]);
       const double F01 = fma(ih, fma(s, e2.x, d30.x), Fb[1]);
       const double F11 = fma(ih, fma(s, e2.y, d30.y), Fb[3]);
-      const NH2<double> q = nh2_eval(F00, F01, F10, F11, lam, mu);
-      bad += (q.J > 0.0) ? 0.0 : 1.0;
-      const double P00 = fma(mu, F00, q.hb * q.f00), P01 = fma(mu, F01, q.hb * q.f01);
-      const double P10 = fma(mu, F10, q.hb * q.f10), P11 = fma(mu, F11, q.hb * q.f11);
+      double P00, P01, P10, P11;
+      const double J = law2_P<LAW, double>(F00, F01, F10, F11, lam, mu, P00, P01, P10, P11);
+      bad += (J > 0.0) ? 0.0 : 1.0;
       Psum[0] += P00;
       Psum[1] += P01;
       Psum[2] += P10;
@@ -252,7 +286,9 @@ __device__ __forceinline__ void element_residual(int e, int n, const double2* w,
   stage_f[7 * NN + e] = k * (-Sa1y + Sb0y);
 }
 
-// Psi = lam/4 (J^2-1) - (lam/2+mu) ln J + mu/2 (|F|^2 - 2) summed over the element's Gauss points.
+// Psi summed over the element's Gauss points: neo-Hookean lam/4 (J^2-1) - (lam/2+mu) ln J +
+// mu/2 (|F|^2 - 2), or St. Venant-Kirchhoff lam/2 (tr E)^2 + mu E:E.
+template <int LAW>
 __device__ __forceinline__ double element_energy(int e, int n, const double2* w, const double* Fb, double lam,
                                                  double mu) {
   const int i = e % n, j = e / n, ip = (i + 1) % n, jp = (j + 1) % n;
@@ -269,17 +305,27 @@ __device__ __forceinline__ double element_energy(int e, int n, const double2* w,
       const double F10 = Fb[2] + ih * ((1 - t) * (w1.y - w0.y) + t * (w2.y - w3.y));
       const double F01 = Fb[1] + ih * ((1 - s) * (w3.x - w0.x) + s * (w2.x - w1.x));
       const double F11 = Fb[3] + ih * ((1 - s) * (w3.y - w0.y) + s * (w2.y - w1.y));
-      const double J = F00 * F11 - F01 * F10;
-      const double trC = F00 * F00 + F01 * F01 + F10 * F10 + F11 * F11;
-      acc += 0.25 * lam * (J * J - 1.0) - (0.5 * lam + mu) * log(J) + 0.5 * mu * (trC - 2.0);
+      if constexpr (LAW == kLawNH) {
+        const double J = F00 * F11 - F01 * F10;
+        const double trC = F00 * F00 + F01 * F01 + F10 * F10 + F11 * F11;
+        acc += 0.25 * lam * (J * J - 1.0) - (0.5 * lam + mu) * log(J) + 0.5 * mu * (trC - 2.0);
+      } else {
+        const double E00 = 0.5 * (F00 * F00 + F10 * F10 - 1.0), E11 = 0.5 * (F01 * F01 + F11 * F11 - 1.0);
+        const double E01 = 0.5 * (F00 * F01 + F10 * F11), trE = E00 + E11;
+        acc += 0.5 * lam * trE * trE + mu * (E00 * E00 + E11 * E11 + 2.0 * E01 * E01);
+      }
     }
   }
   return acc;
 }
 
 // ------------------------------------------------------------------ tangent (TA)
-// Element tangent Ke (36 upper-triangle entries) into stage[tri][slot].
-template <typename TA>
+// Element tangent Ke (36 upper-triangle entries) into stage[tri][slot]:
+//   K_(a,i)(b,k) = sum_qp wq g_a,J A_iJkL g_b,L.
+// Neo-Hookean: mu d_ik g_a.g_b + gm v_a,i v_b,k - hb v_b,i v_a,k with v = F^-T g.
+// St. Venant-Kirchhoff (A = d_ik S_JL + F_iI F_kK CC_IJKL, CC = lam 1(x)1 + 2 mu I^sym):
+//   d_ik g_a.S.g_b + lam v_a,i v_b,k + mu [(g_a.g_b) (F F^T)_ik + v_b,i v_a,k] with v = F g.
+template <typename TA, int LAW>
 __device__ __forceinline__ void element_tangent(int e, int n, const vec2_t<TA>* w, const TA* Fb, TA lam, TA mu,
                                                 TA* stage_k, int slot, int NN) {
   const int i = e % n, j = e / n, ip = (i + 1) % n, jp = (j + 1) % n;
@@ -302,27 +348,56 @@ __device__ __forceinline__ void element_tangent(int e, int n, const vec2_t<TA>* 
       const TA F10 = Fb[2] + ih * (d10y + t * e1y);
       const TA F01 = Fb[1] + ih * (d30x + s * e2x);
       const TA F11 = Fb[3] + ih * (d30y + s * e2y);
-      const NH2<TA> q = nh2_eval(F00, F01, F10, F11, lam, mu);
-      // physical shape gradients g_a and v_a = Fit g_a
+      // physical shape gradients g_a
       TA gx_[4] = {-(1 - t) * ih, (1 - t) * ih, t * ih, -t * ih};
       TA gy_[4] = {-(1 - s) * ih, -s * ih, s * ih, (1 - s) * ih};
       TA vx[4], vy[4];
+      if constexpr (LAW == kLawNH) {
+        const NH2<TA> q = nh2_eval(F00, F01, F10, F11, lam, mu);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        vx[a] = q.f00 * gx_[a] + q.f01 * gy_[a];
-        vy[a] = q.f10 * gx_[a] + q.f11 * gy_[a];
-      }
-      const TA cm = wq * mu, cg = wq * q.gm, ch = wq * q.hb;
+        for (int a = 0; a < 4; ++a) {  // v_a = Fit g_a
+          vx[a] = q.f00 * gx_[a] + q.f01 * gy_[a];
+          vy[a] = q.f10 * gx_[a] + q.f11 * gy_[a];
+        }
+        const TA cm = wq * mu, cg = wq * q.gm, ch = wq * q.hb;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < 8; ++r) {
 #pragma unroll
-        for (int c = r; c < 8; ++c) {
-          const int a = r >> 1, ii = r & 1, b = c >> 1, kk = c & 1;
-          const TA va_i = ii ? vy[a] : vx[a], va_k = kk ? vy[a] : vx[a];
-          const TA vb_i = ii ? vy[b] : vx[b], vb_k = kk ? vy[b] : vx[b];
-          TA val = cg * va_i * vb_k - ch * vb_i * va_k;
-          if (ii == kk) val += cm * (gx_[a] * gx_[b] + gy_[a] * gy_[b]);
-          Ke[tri8(r, c)] += val;
+          for (int c = r; c < 8; ++c) {
+            const int a = r >> 1, ii = r & 1, b = c >> 1, kk = c & 1;
+            const TA va_i = ii ? vy[a] : vx[a], va_k = kk ? vy[a] : vx[a];
+            const TA vb_i = ii ? vy[b] : vx[b], vb_k = kk ? vy[b] : vx[b];
+            TA val = cg * va_i * vb_k - ch * vb_i * va_k;
+            if (ii == kk) val += cm * (gx_[a] * gx_[b] + gy_[a] * gy_[b]);
+            Ke[tri8(r, c)] += val;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {  // v_a = F g_a
+          vx[a] = F00 * gx_[a] + F01 * gy_[a];
+          vy[a] = F10 * gx_[a] + F11 * gy_[a];
+        }
+        const TA c00 = F00 * F00 + F10 * F10, c01 = F00 * F01 + F10 * F11, c11 = F01 * F01 + F11 * F11;
+        const TA trE = TA(0.5) * (c00 + c11) - TA(1);
+        const TA S00 = wq * (lam * trE + mu * (c00 - TA(1))), S11 = wq * (lam * trE + mu * (c11 - TA(1)));
+        const TA S01 = wq * mu * c01;
+        const TA b00 = F00 * F00 + F01 * F01, b01 = F00 * F10 + F01 * F11, b11 = F10 * F10 + F11 * F11;
+        const TA cl = wq * lam, cm = wq * mu;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+#pragma unroll
+          for (int c = r; c < 8; ++c) {
+            const int a = r >> 1, ii = r & 1, b = c >> 1, kk = c & 1;
+            const TA va_i = ii ? vy[a] : vx[a], va_k = kk ? vy[a] : vx[a];
+            const TA vb_i = ii ? vy[b] : vx[b], vb_k = kk ? vy[b] : vx[b];
+            const TA gg = gx_[a] * gx_[b] + gy_[a] * gy_[b];
+            const TA bik = (ii == kk) ? (ii ? b11 : b00) : b01;
+            TA val = cl * va_i * vb_k + cm * (gg * bik + vb_i * va_k);
+            if (ii == kk)
+              val += gx_[a] * (S00 * gx_[b] + S01 * gy_[b]) + gy_[a] * (S01 * gx_[b] + S11 * gy_[b]);
+            Ke[tri8(r, c)] += val;
+          }
         }
       }
     }
@@ -484,7 +559,7 @@ __device__ __forceinline__ void invert_block(const TA (&Kself)[4], bool pinned, 
 //    element matrices (needed only while building) in the block's global scratch.
 template <typename TA>
 struct MgLevel {
-  int n, NN;
+  int n, NN, bc;
   TA* st;          // [36][NN]
   TA* mi;          // [4][NN]
   vec2_t<TA>* r;   // [NN]
@@ -497,6 +572,8 @@ template <typename TA>
 struct MgCtx {
   int levels;  // coarse levels, 0 = off
   int n;       // fine grid
+  int bc;      // pinned nodes of every level: as on the fine grid (pinned2)
+  TA omega;    // smoother damping
   TA* fast;
   TA* slow;
   // fine-level residual (restriction input), at the start of the fast region
@@ -513,6 +590,7 @@ struct MgCtx {
     }
     v.n = n >> l;
     v.NN = v.n * v.n;
+    v.bc = bc;
     v.ke = k;
     if (l < levels) {
       v.st = f;
@@ -604,7 +682,7 @@ __device__ __forceinline__ vec2_t<TA> mg_apply(const MgLevel<TA>& L, const vec2_
     yx += L.st[(size_t)(nb * 4 + 0) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 1) * L.NN + v] * zn.y;
     yy += L.st[(size_t)(nb * 4 + 2) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 3) * L.NN + v] * zn.y;
   }
-  return v == 0 ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(yx, yy);
+  return pinned2(i, j, L.bc) ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(yx, yy);
 }
 
 template <typename TA>
@@ -616,7 +694,7 @@ __device__ __forceinline__ vec2_t<TA> mg_smooth(const TA* mi, int NN, int v, vec
 // Full-weighting restriction (the transpose of bilinear prolongation) of the fine vector t
 // (grid nf) to coarse node (I, J); zero at the pinned node.
 template <typename TA>
-__device__ __forceinline__ vec2_t<TA> mg_restrict(const vec2_t<TA>* t, int nf, int I, int J) {
+__device__ __forceinline__ vec2_t<TA> mg_restrict(const vec2_t<TA>* t, int nf, int I, int J, int bc) {
   const int ix = 2 * I, jy = 2 * J;
   const int cols[3] = {wrap_dec(ix, nf), ix, ix + 1};
   const int rows[3] = {wrap_dec(jy, nf) * nf, jy * nf, (jy + 1) * nf};
@@ -630,7 +708,7 @@ __device__ __forceinline__ vec2_t<TA> mg_restrict(const vec2_t<TA>* t, int nf, i
       sx += wgt * v.x;
       sy += wgt * v.y;
     }
-  return (I == 0 && J == 0) ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(sx, sy);
+  return pinned2(I, J, bc) ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(sx, sy);
 }
 
 // Bilinear prolongation of the coarse vector zc (grid nf/2) to fine node (i, j) of grid nf.
@@ -702,7 +780,7 @@ __device__ __forceinline__ void mg_build_part2(const MgCtx<TA>& mg) {
         for (int q = 0; q < 4; ++q) v.st[(size_t)(nb * 4 + q) * v.NN + node] = blk[q];
         if (nb == 4) {
           TA m[4];
-          invert_block<TA>(blk, node == 0, m);
+          invert_block<TA>(blk, pinned2(i, j, v.bc), m);
 #pragma unroll
           for (int q = 0; q < 4; ++q) v.mi[(size_t)q * v.NN + node] = m[q];
         }
@@ -729,11 +807,12 @@ __device__ __forceinline__ void mg_build_part2(const MgCtx<TA>& mg) {
           A[(size_t)tid * ld + 2 * nm + kk] += c.ke[(size_t)tri8(2 * l + ii, 2 * m + kk) * c.NN + slot];
       }
     }
-    if (tid < 2) {
+    // pinned rows: identity; pinned columns of the other rows: zero
+    if (pinned2(ni, nj, c.bc)) {
       for (int q = 0; q < D; ++q) A[(size_t)tid * ld + q] = q == tid ? TA(1) : TA(0);
     } else {
-      A[(size_t)tid * ld] = TA(0);
-      A[(size_t)tid * ld + 1] = TA(0);
+      for (int q = 0; q < D; q += 2)
+        if (pinned2((q >> 1) % c.n, (q >> 1) / c.n, c.bc)) A[(size_t)tid * ld + q] = A[(size_t)tid * ld + q + 1] = TA(0);
     }
   }
   __syncthreads();
@@ -763,9 +842,9 @@ __device__ __forceinline__ void mg_build_part2(const MgCtx<TA>& mg) {
 template <typename TA>
 __device__ __forceinline__ void mg_restrict_smooth(const MgCtx<TA>& mg, int l, const vec2_t<TA>* tf, int nf, int t) {
   const MgLevel<TA> c = mg.level(l);
-  const vec2_t<TA> r = mg_restrict<TA>(tf, nf, t % c.n, t / c.n);
+  const vec2_t<TA> r = mg_restrict<TA>(tf, nf, t % c.n, t / c.n, mg.bc);
   c.r[t] = r;
-  if (l < mg.levels) c.z[t] = mg_smooth<TA>(c.mi, c.NN, t, r, (TA)kMgOmega);
+  if (l < mg.levels) c.z[t] = mg_smooth<TA>(c.mi, c.NN, t, r, mg.omega);
 }
 
 // Where the corrected z of level l ends: the t vector of a smoothing level (free on the way
@@ -784,7 +863,7 @@ __device__ __forceinline__ const vec2_t<TA>* mg_result(const MgCtx<TA>& mg, int 
 template <typename TA>
 __device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
   const int tid = threadIdx.x;
-  const TA om = (TA)kMgOmega;
+  const TA om = mg.omega;
   for (int l = 1; l < mg.levels; ++l) {  // descend: residual, restrict (+ next pre-smoothing)
     const MgLevel<TA> v = mg.level(l);
     if (tid < v.NN) {
@@ -805,7 +884,8 @@ __device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
       for (int q = l16; q < D; q += 16) zz += A[(size_t)row * ld + q] * r[q];
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
-    if (row < D && l16 == 0) reinterpret_cast<TA*>(c.z)[row] = row < 2 ? TA(0) : zz;
+    if (row < D && l16 == 0)
+      reinterpret_cast<TA*>(c.z)[row] = pinned2((row >> 1) % c.n, (row >> 1) / c.n, c.bc) ? TA(0) : zz;
     __syncthreads();
   }
   for (int l = mg.levels - 1; l >= 1; --l) {  // ascend: prolong, post-smooth into t
@@ -876,7 +956,8 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
     __syncthreads();
     if (o.active) {
       apply_pair<TA, REG>(S, o, ps, u, w);
-      if (o.node[0] == 0) w[0] = w[1] = TA(0);  // pinned node
+      if (o.pin[0]) w[0] = w[1] = TA(0);  // pinned nodes
+      if (o.pin[1]) w[2] = w[3] = TA(0);
     } else {
       w[0] = w[1] = w[2] = w[3] = TA(0);
     }
@@ -895,7 +976,7 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
       jacobi(r, TA(1));
       return;
     }
-    const TA om = (TA)kMgOmega;
+    const TA om = mg.omega;
     jacobi(r, om);     // pre-smoothing from zero
     exchange_apply();  // w = K u
     vec2_t<TA>* ft = mg.fine_t();
@@ -999,7 +1080,7 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
 // Minv (inverted nodal blocks, zero on idle threads and the pinned node) stays in
 // registers; with withL the condensation right-hand sides go to shared memory,
 // Lb[c][NN] = -L_c of each owned node.
-template <typename TA, bool REG, bool kMG>
+template <typename TA, bool REG, bool kMG, int LAW>
 __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& sm, TA* stage_k,
                                               const TA (&Fb)[4], const uint8_t* phase, Stencil<TA, REG>& S,
                                               TA (&Minv)[2][4], bool withL, vec2_t<TA>* Lb, const MgCtx<TA>& mg) {
@@ -1016,7 +1097,7 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
     for (int s = 0; s < 2; ++s) {
       const int e = o.node[s];
       const int ph = phase[e];
-      element_tangent<TA>(e, n, wsrc, Fb, (TA)sm.lame[2 * ph], (TA)sm.lame[2 * ph + 1], stage_k, e, NN);
+      element_tangent<TA, LAW>(e, n, wsrc, Fb, (TA)sm.lame[2 * ph], (TA)sm.lame[2 * ph + 1], stage_k, e, NN);
     }
   }
   __syncthreads();
@@ -1053,7 +1134,7 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
     }
     TA self[4] = {Kn[4][0], Kn[4][1], Kn[4][2], Kn[4][3]};
     TA mi[4];
-    invert_block<TA>(self, !o.active || o.node[s] == 0, mi);
+    invert_block<TA>(self, !o.active || o.pin[s], mi);
 #pragma unroll
     for (int c = 0; c < 4; ++c) Minv[s][c] = mi[c];
     if (withL) {
@@ -1070,7 +1151,7 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
       {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const bool pinned = o.node[s] == 0;
+          const bool pinned = o.pin[s];
           Lb[c * o.NN + o.node[s]] = mk2<TA>(pinned ? TA(0) : -L[s][0][c], pinned ? TA(0) : -L[s][1][c]);
         }
       }
@@ -1081,7 +1162,10 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
 
 // Energy form of the tangent transfer over this thread's two elements (FP64 sums of
 // per-element TA partials).  X: [4][NN] periodic responses to the unit gradients.
-template <typename TA>
+// G_c : A : G_d with M_c = Fit^T G_c (neo-Hookean): mu G_c:G_d - hb tr(M_c M_d) + gm tr M_c tr M_d;
+// with M_c = F^T G_c (St. Venant-Kirchhoff): tr(G_c S G_d^T) + lam tr M_c tr M_d
+// + mu [M_c:M_d + tr(M_c M_d)].
+template <typename TA, int LAW>
 __device__ __forceinline__ void element_transfer(int e, int n, const vec2_t<TA>* wsrc, const vec2_t<TA>* X,
                                                  const TA (&Fb)[4], TA lam, TA mu, double (&Q)[10]) {
   const int NN = n * n;
@@ -1108,9 +1192,29 @@ __device__ __forceinline__ void element_transfer(int e, int n, const vec2_t<TA>*
       const TA F10 = Fb[2] + ih * ((1 - t) * (w1.y - w0.y) + t * (w2.y - w3.y));
       const TA F01 = Fb[1] + ih * ((1 - s) * (w3.x - w0.x) + s * (w2.x - w1.x));
       const TA F11 = Fb[3] + ih * ((1 - s) * (w3.y - w0.y) + s * (w2.y - w1.y));
-      const NH2<TA> nh = nh2_eval(F00, F01, F10, F11, lam, mu);
+      // K = Fit (neo-Hookean) or F (St. Venant-Kirchhoff) for M_c = K^T G_c
+      TA k00, k01, k10, k11, hb = TA(0), gm = TA(0), S00 = TA(0), S01 = TA(0), S11 = TA(0);
+      if constexpr (LAW == kLawNH) {
+        const NH2<TA> nh = nh2_eval(F00, F01, F10, F11, lam, mu);
+        k00 = nh.f00;
+        k01 = nh.f01;
+        k10 = nh.f10;
+        k11 = nh.f11;
+        hb = nh.hb;
+        gm = nh.gm;
+      } else {
+        k00 = F00;
+        k01 = F01;
+        k10 = F10;
+        k11 = F11;
+        const TA c00 = F00 * F00 + F10 * F10, c01 = F00 * F01 + F10 * F11, c11 = F01 * F01 + F11 * F11;
+        const TA trE = TA(0.5) * (c00 + c11) - TA(1);
+        S00 = lam * trE + mu * (c00 - TA(1));
+        S11 = lam * trE + mu * (c11 - TA(1));
+        S01 = mu * c01;
+      }
       TA G[4][4];  // G_c = E_c + Grad X_c, row-major 2x2
-      TA M[4][4];  // M_c = Fit^T G_c
+      TA M[4][4];  // M_c = K^T G_c
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const vec2_t<TA> a0 = x[c][0], a1 = x[c][1], a2 = x[c][2], a3 = x[c][3];
@@ -1119,22 +1223,30 @@ __device__ __forceinline__ void element_transfer(int e, int n, const vec2_t<TA>*
         G[c][1] = ih * ((1 - s) * (a3.x - a0.x) + s * (a2.x - a1.x));
         G[c][3] = ih * ((1 - s) * (a3.y - a0.y) + s * (a2.y - a1.y));
         G[c][c] += TA(1);
-        // M_LJ = sum_i Fit_iL G_iJ
-        M[c][0] = nh.f00 * G[c][0] + nh.f10 * G[c][2];
-        M[c][1] = nh.f00 * G[c][1] + nh.f10 * G[c][3];
-        M[c][2] = nh.f01 * G[c][0] + nh.f11 * G[c][2];
-        M[c][3] = nh.f01 * G[c][1] + nh.f11 * G[c][3];
+        // M_LJ = sum_i K_iL G_iJ
+        M[c][0] = k00 * G[c][0] + k10 * G[c][2];
+        M[c][1] = k00 * G[c][1] + k10 * G[c][3];
+        M[c][2] = k01 * G[c][0] + k11 * G[c][2];
+        M[c][3] = k01 * G[c][1] + k11 * G[c][3];
       }
       int k = 0;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int d = c; d < 4; ++d) {
-          const TA gg = G[c][0] * G[d][0] + G[c][1] * G[d][1] + G[c][2] * G[d][2] + G[c][3] * G[d][3];
           // tr(M_c M_d)
           const TA tm = M[c][0] * M[d][0] + M[c][1] * M[d][2] + M[c][2] * M[d][1] + M[c][3] * M[d][3];
           const TA ac = M[c][0] + M[c][3], ad = M[d][0] + M[d][3];
-          q[k++] += wq * (mu * gg - nh.hb * tm + nh.gm * ac * ad);
+          if constexpr (LAW == kLawNH) {
+            const TA gg = G[c][0] * G[d][0] + G[c][1] * G[d][1] + G[c][2] * G[d][2] + G[c][3] * G[d][3];
+            q[k++] += wq * (mu * gg - hb * tm + gm * ac * ad);
+          } else {
+            const TA mm = M[c][0] * M[d][0] + M[c][1] * M[d][1] + M[c][2] * M[d][2] + M[c][3] * M[d][3];
+            // tr(G_c S G_d^T) = sum_i (G_c S)_iL G_d,iL
+            const TA gs = (G[c][0] * S00 + G[c][1] * S01) * G[d][0] + (G[c][0] * S01 + G[c][1] * S11) * G[d][1] +
+                          (G[c][2] * S00 + G[c][3] * S01) * G[d][2] + (G[c][2] * S01 + G[c][3] * S11) * G[d][3];
+            q[k++] += wq * (gs + lam * ac * ad + mu * (mm + tm));
+          }
         }
     }
   }
@@ -1144,14 +1256,14 @@ __device__ __forceinline__ void element_transfer(int e, int n, const vec2_t<TA>*
 
 // kFixed: one grid size for the whole batch, arrays indexed arithmetically (qp -> RVE qp or 0,
 // fluctuation of qp at qp*2*n*n) instead of through the context's index tables.
-template <typename TA, bool kFixed, bool kMG>
+template <typename TA, bool kFixed, bool kMG, int LAW>
 __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, TA* gscr) {
   constexpr bool REG = std::is_same<TA, float>::value;
   const int tid = threadIdx.x;
   const int rv = kFixed ? (a.phase_per_qp ? qp : 0) : a.qp_rve[qp];
   const int n = kFixed ? a.fixed_n : a.rve_n[rv];
   const int NN = n * n;
-  const Own2D o = make_own(n);
+  const Own2D o = make_own(n, a.bc);
   const uint8_t* phase = a.phase + (kFixed ? (size_t)rv * n * n : (size_t)a.rve_phase_off[rv]);
   const size_t w_off = kFixed ? (size_t)qp * 2 * n * n : (size_t)a.qp_w_off[qp];
   const double* w_in = a.w_in + w_off;
@@ -1172,7 +1284,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   if (tid < 2 * kMaxPhase) sm.lame[tid] = a.rve_lame[(size_t)rv * 2 * kMaxPhase + tid];
   for (int v = tid; v < NN; v += blockDim.x) {
     double2 wv = make_double2(w_in[2 * v], w_in[2 * v + 1]);
-    if (v == 0) wv = make_double2(0.0, 0.0);
+    if (pinned2(v % n, v / n, a.bc)) wv = make_double2(0.0, 0.0);
     sm.w[v] = wv;
     if constexpr (REG) sm.w32[v] = make_float2((float)wv.x, (float)wv.y);
   }
@@ -1189,6 +1301,8 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   MgCtx<TA> mg;
   mg.n = n;
   mg.levels = (kMG && a.mg) ? mg_levels(n) : 0;
+  mg.bc = a.bc;
+  mg.omega = (TA)a.mg_omega;
   if constexpr (REG) {
     mg.fast = reinterpret_cast<TA*>(sm.stage + 8 * (size_t)NN * sizeof(vec2_t<TA>));
     mg.slow = reinterpret_cast<TA*>(a.scratch) + (size_t)blockIdx.x * a.scratch_stride;
@@ -1229,7 +1343,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
         for (int s = 0; s < 2; ++s) {
           const int e = o.node[s];
           const int ph = phase[e];
-          element_residual(e, n, sm.w, sm.misc, sm.lame[2 * ph], sm.lame[2 * ph + 1], stage_f, Psum, bad);
+          element_residual<LAW>(e, n, sm.w, sm.misc, sm.lame[2 * ph], sm.lame[2 * ph + 1], stage_f, Psum, bad);
         }
       }
       __syncthreads();
@@ -1243,7 +1357,8 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
           R[2 * s] = stage_f[0 * NN + eA] + stage_f[2 * NN + eB] + stage_f[4 * NN + eC] + stage_f[6 * NN + eD];
           R[2 * s + 1] = stage_f[1 * NN + eA] + stage_f[3 * NN + eB] + stage_f[5 * NN + eC] + stage_f[7 * NN + eD];
         }
-        if (o.node[0] == 0) R[0] = R[1] = 0.0;
+        if (o.pin[0]) R[0] = R[1] = 0.0;
+        if (o.pin[1]) R[2] = R[3] = 0.0;
       }
       double v2[2] = {R[0] * R[0] + R[1] * R[1] + R[2] * R[2] + R[3] * R[3], bad};
       block_sum<2, double>(v2, sm.red + (it & 1) * 512);
@@ -1287,7 +1402,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       // ---- tangent and PCG correction
       {
         const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
-        build_tangent<TA, REG, kMG>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb, mg);
+        build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb, mg);
       }
       TA b[4];
 #pragma unroll
@@ -1351,7 +1466,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
     for (int s = 0; s < 2; ++s) {
       const int e = o.node[s];
       const int ph = phase[e];
-      Pv[4] += element_energy(e, n, sm.w, sm.misc, sm.lame[2 * ph], sm.lame[2 * ph + 1]);
+      Pv[4] += element_energy<LAW>(e, n, sm.w, sm.misc, sm.lame[2 * ph], sm.lame[2 * ph + 1]);
     }
   }
   // the last residual norm used buffer (it & 1) and may still be read: use the other one
@@ -1367,7 +1482,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   const bool want_A = usable && !(a.flags & kFlagNoTangent) && a.A != nullptr;
   if (want_A) {
     const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
-    build_tangent<TA, REG, kMG>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb, mg);
+    build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb, mg);
     vec2_t<TA>* X = Xs;
     for (int c = 0; c < 4; ++c) {
       TA b[4] = {TA(0), TA(0), TA(0), TA(0)};
@@ -1399,7 +1514,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       for (int s = 0; s < 2; ++s) {
         const int e = o.node[s];
         const int ph = phase[e];
-        element_transfer<TA>(e, n, wsrc, X, Fb, (TA)sm.lame[2 * ph], (TA)sm.lame[2 * ph + 1], Q);
+        element_transfer<TA, LAW>(e, n, wsrc, X, Fb, (TA)sm.lame[2 * ph], (TA)sm.lame[2 * ph + 1], Q);
       }
     }
     block_sum<10, double>(Q, sm.red + (it & 1) * 512);
@@ -1438,7 +1553,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   __syncthreads();
 }
 
-template <typename TA, bool kFixed, bool kMG>
+template <typename TA, bool kFixed, bool kMG, int LAW>
 __global__ void __launch_bounds__(kThreads2D, 1) rve2d_kernel(const Rve2dArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem2D<TA> sm;
@@ -1452,19 +1567,19 @@ __global__ void __launch_bounds__(kThreads2D, 1) rve2d_kernel(const Rve2dArgs a)
     const int item = s_item;
     __syncthreads();
     if (item >= (a.n_dev ? *a.n_dev : a.n_qp)) break;
-    solve_item_2d<TA, kFixed, kMG>(a, kFixed ? item : a.order[item], sm, gscr);
+    solve_item_2d<TA, kFixed, kMG, LAW>(a, kFixed ? item : a.order[item], sm, gscr);
   }
 }
 
 }  // namespace
 
 // Launch of one instantiation (grid of n_blocks persistent blocks, smem dynamic shared bytes).
-template <typename TA, bool kFixed, bool kMG>
+template <typename TA, bool kFixed, bool kMG, int LAW>
 inline cudaError_t rve2d_launch_instance(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream) {
-  const cudaError_t err =
-      cudaFuncSetAttribute(rve2d_kernel<TA, kFixed, kMG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t err = cudaFuncSetAttribute(rve2d_kernel<TA, kFixed, kMG, LAW>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  rve2d_kernel<TA, kFixed, kMG><<<n_blocks, kThreads2D, smem, stream>>>(a);
+  rve2d_kernel<TA, kFixed, kMG, LAW><<<n_blocks, kThreads2D, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,8 @@
+// 2D RVE kernel instantiation: FP64, block-Jacobi, neo-Hookean, fixed single-grid layout (no-allocation entry).
+#include "rve2d.cuh"
+
+namespace fehmm {
+cudaError_t rve2d_launch_fp64_fixed_nh(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream) {
+  return rve2d_launch_instance<double, true, false, 0>(a, n_blocks, smem, stream);
+}
+}  // namespace fehmm

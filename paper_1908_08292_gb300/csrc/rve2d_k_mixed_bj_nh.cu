@@ -1,0 +1,8 @@
+// 2D RVE kernel instantiation: mixed precision, block-Jacobi, neo-Hookean.
+#include "rve2d.cuh"
+
+namespace fehmm {
+cudaError_t rve2d_launch_mixed_bj_nh(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream) {
+  return rve2d_launch_instance<float, false, false, 0>(a, n_blocks, smem, stream);
+}
+}  // namespace fehmm

@@ -37,14 +37,28 @@ namespace fehmm {
 namespace {
 
 constexpr int kThreads3D = 512;
-constexpr int kQp3 = 12;  // per Gauss point: Fit (9), hb, gm, padding (vector loads)
+// Gauss-point data per law: neo-Hookean Fit (9), hb, gm, padding (12); St. Venant-Kirchhoff F (9),
+// S (6: 00, 01, 02, 11, 12, 22), padding (16).  Scratch is sized for the larger.
+constexpr int kLawNH = 0, kLawSVK = 1;
+template <int LAW>
+__host__ __device__ constexpr int qp_vals() { return LAW == kLawNH ? 12 : 16; }
+constexpr int kQp3Max = 16;
 
-// Gauss-point data layout [8 qp][12 values][NE] grouped into 4-wide vectors so that a thread
-// loads its element's data with 3 float4 (FP32) or 6 double2 (FP64) loads, coalesced over e.
-__device__ __forceinline__ void load_qp(const float* qpd, int NE, int q, int e, float (&d)[12]) {
-  const float4* b = reinterpret_cast<const float4*>(qpd) + (size_t)(q * 3) * NE + e;
+// Pinned nodes of the fluctuation: node 0 (periodic coupling) or every node on the lattice
+// planes i = 0, j = 0 or k = 0 (KUBC: the cell boundary).
+__device__ __forceinline__ bool pinned3(int v, int n, int bc) {
+  if (!bc) return v == 0;
+  const int i = v % n, j = (v / n) % n, k = v / (n * n);
+  return i == 0 || j == 0 || k == 0;
+}
+
+// Gauss-point data layout [8 qp][NQ values][NE] grouped into 4-wide vectors so that a thread
+// loads its element's data with NQ/4 float4 (FP32) or NQ/2 double2 (FP64) loads, coalesced over e.
+template <int NQ>
+__device__ __forceinline__ void load_qp(const float* qpd, int NE, int q, int e, float (&d)[NQ]) {
+  const float4* b = reinterpret_cast<const float4*>(qpd) + (size_t)(q * (NQ / 4)) * NE + e;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
+  for (int j = 0; j < NQ / 4; ++j) {
     const float4 v = b[(size_t)j * NE];
     d[4 * j] = v.x;
     d[4 * j + 1] = v.y;
@@ -52,24 +66,27 @@ __device__ __forceinline__ void load_qp(const float* qpd, int NE, int q, int e, 
     d[4 * j + 3] = v.w;
   }
 }
-__device__ __forceinline__ void load_qp(const double* qpd, int NE, int q, int e, double (&d)[12]) {
-  const double2* b = reinterpret_cast<const double2*>(qpd) + (size_t)(q * 6) * NE + e;
+template <int NQ>
+__device__ __forceinline__ void load_qp(const double* qpd, int NE, int q, int e, double (&d)[NQ]) {
+  const double2* b = reinterpret_cast<const double2*>(qpd) + (size_t)(q * (NQ / 2)) * NE + e;
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
+  for (int j = 0; j < NQ / 2; ++j) {
     const double2 v = b[(size_t)j * NE];
     d[2 * j] = v.x;
     d[2 * j + 1] = v.y;
   }
 }
-__device__ __forceinline__ void store_qp(float* qpd, int NE, int q, int e, const float (&d)[12]) {
-  float4* b = reinterpret_cast<float4*>(qpd) + (size_t)(q * 3) * NE + e;
+template <int NQ>
+__device__ __forceinline__ void store_qp(float* qpd, int NE, int q, int e, const float (&d)[NQ]) {
+  float4* b = reinterpret_cast<float4*>(qpd) + (size_t)(q * (NQ / 4)) * NE + e;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) b[(size_t)j * NE] = make_float4(d[4 * j], d[4 * j + 1], d[4 * j + 2], d[4 * j + 3]);
+  for (int j = 0; j < NQ / 4; ++j) b[(size_t)j * NE] = make_float4(d[4 * j], d[4 * j + 1], d[4 * j + 2], d[4 * j + 3]);
 }
-__device__ __forceinline__ void store_qp(double* qpd, int NE, int q, int e, const double (&d)[12]) {
-  double2* b = reinterpret_cast<double2*>(qpd) + (size_t)(q * 6) * NE + e;
+template <int NQ>
+__device__ __forceinline__ void store_qp(double* qpd, int NE, int q, int e, const double (&d)[NQ]) {
+  double2* b = reinterpret_cast<double2*>(qpd) + (size_t)(q * (NQ / 2)) * NE + e;
 #pragma unroll
-  for (int j = 0; j < 6; ++j) b[(size_t)j * NE] = make_double2(d[2 * j], d[2 * j + 1]);
+  for (int j = 0; j < NQ / 2; ++j) b[(size_t)j * NE] = make_double2(d[2 * j], d[2 * j + 1]);
 }
 
 __device__ __forceinline__ double g01(int g) { return g == 0 ? 0.21132486540518711775 : 0.78867513459481288225; }
@@ -126,6 +143,59 @@ __device__ __forceinline__ void tangent_action(const T* Fit, T hb, T gm, T mu, c
     for (int J = 0; J < 3; ++J) {
       const T t = Fit[3 * i + 0] * U[0 * 3 + J] + Fit[3 * i + 1] * U[1 * 3 + J] + Fit[3 * i + 2] * U[2 * 3 + J];
       dP[3 * i + J] = mu * dF[3 * i + J] - hb * t + ga * Fit[3 * i + J];
+    }
+}
+
+// St. Venant-Kirchhoff (S = lam tr(E) I + 2 mu E, E = (F^T F - I)/2): S as 6 values (00, 01, 02,
+// 11, 12, 22).
+template <typename T>
+__device__ __forceinline__ void svk3_S(const T* F, T lam, T mu, T (&S6)[6]) {
+  T C[6];  // C = F^T F, same order
+  const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) C[k] = F[I6[k]] * F[J6[k]] + F[3 + I6[k]] * F[3 + J6[k]] + F[6 + I6[k]] * F[6 + J6[k]];
+  const T trE = T(0.5) * (C[0] + C[3] + C[5]) - T(1.5);
+  S6[0] = lam * trE + mu * (C[0] - T(1));
+  S6[3] = lam * trE + mu * (C[3] - T(1));
+  S6[5] = lam * trE + mu * (C[5] - T(1));
+  S6[1] = mu * C[1];
+  S6[2] = mu * C[2];
+  S6[4] = mu * C[4];
+}
+
+// symmetric 3x3 entry (I, J) of 6 stored values
+template <typename T>
+__device__ __forceinline__ T sym6(const T (&S6)[6], int I, int J) {
+  const int a = I < J ? I : J, b = I < J ? J : I;
+  return S6[a == 0 ? b : (a == 1 ? 2 + b : 5)];
+}
+
+// St. Venant-Kirchhoff tangent action: dP = dF S + F dS, dS = lam tr(U) I + mu (U + U^T), U = F^T dF.
+template <typename T>
+__device__ __forceinline__ void svk_tangent_action(const T* F, const T* S6p, T lam, T mu, const T (&dF)[9],
+                                                   T (&dP)[9]) {
+  T S6[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) S6[k] = S6p[k];
+  T U[9];
+#pragma unroll
+  for (int I = 0; I < 3; ++I)
+#pragma unroll
+    for (int J = 0; J < 3; ++J) U[3 * I + J] = F[I] * dF[J] + F[3 + I] * dF[3 + J] + F[6 + I] * dF[6 + J];
+  const T lt = lam * (U[0] + U[4] + U[8]);
+  T dS[9];
+#pragma unroll
+  for (int I = 0; I < 3; ++I)
+#pragma unroll
+    for (int J = 0; J < 3; ++J) dS[3 * I + J] = mu * (U[3 * I + J] + U[3 * J + I]) + (I == J ? lt : T(0));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int J = 0; J < 3; ++J) {
+      T v = T(0);
+#pragma unroll
+      for (int K = 0; K < 3; ++K) v += dF[3 * i + K] * sym6(S6, K, J) + F[3 * i + K] * dS[3 * K + J];
+      dP[3 * i + J] = v;
     }
 }
 
@@ -193,7 +263,7 @@ template <typename TA>
 struct Scratch3 {
   // per-block global scratch, layout set by scratch3_layout
   double* Rf;   // [24][NE] element forces (FP64)
-  TA* qpd;      // [8][kQp3][NE] Gauss-point material data (4-wide groups, see load_qp)
+  TA* qpd;      // [8][qp_vals][NE] Gauss-point material data (4-wide groups, see load_qp)
   TA* x;        // [3][NN] PCG solution
   TA* r;        // [3][NN]
   TA* p;        // [3][NN]
@@ -237,7 +307,7 @@ __host__ __device__ inline long long mg3_elems_max(int nn_max) {
 template <typename TA>
 __host__ __device__ inline size_t scratch3_base_bytes(int NN) {
   const size_t b = sizeof(double) * 24 * (size_t)NN +
-                   sizeof(TA) * ((size_t)kQp3 * 8 * NN + 4 * 3 * (size_t)NN + 6 * (size_t)NN + 27 * (size_t)NN);
+                   sizeof(TA) * ((size_t)kQp3Max * 8 * NN + 4 * 3 * (size_t)NN + 6 * (size_t)NN + 27 * (size_t)NN);
   return (b + 255) & ~size_t(255);
 }
 
@@ -253,7 +323,7 @@ __device__ inline Scratch3<TA> scratch3_layout(unsigned char* base, int NN) {
   s.Rf = reinterpret_cast<double*>(base);
   TA* t = reinterpret_cast<TA*>(base + sizeof(double) * 24 * (size_t)NN);
   s.qpd = t;
-  t += (size_t)kQp3 * 8 * NN;
+  t += (size_t)kQp3Max * 8 * NN;
   s.x = t;
   t += 3 * (size_t)NN;
   s.r = t;
@@ -290,7 +360,7 @@ __device__ __forceinline__ void block_sum_n(T* v, int nv, T* buf) {
 
 template <typename TA>
 struct Mg3Level {
-  int n, NN;
+  int n, NN, bc;
   TA* kb;  // [36 block pairs a <= b][9][NN] element blocks (row-major 3x3)
   TA* mi;  // [6][NN] inverted nodal diagonal blocks (zero at node 0)
   TA* r;   // [3][NN]
@@ -302,6 +372,8 @@ template <typename TA>
 struct Mg3 {
   int levels = 0;  // coarse levels, 0 = block-Jacobi
   int n = 0;       // fine grid
+  int bc = 0;      // pinned nodes of every level as on the fine grid (pinned3)
+  TA omega = TA(0.6);  // smoother damping
   TA* base = nullptr;
   __device__ __forceinline__ Mg3Level<TA> level(int l) const {
     TA* p = base;
@@ -312,6 +384,7 @@ struct Mg3 {
     Mg3Level<TA> v;
     v.n = n >> l;
     v.NN = v.n * v.n * v.n;
+    v.bc = bc;
     v.kb = p;
     v.mi = p + 324 * v.NN;
     v.r = v.mi + 6 * v.NN;
@@ -336,11 +409,12 @@ struct Ctx3 {
   TA* vin;   // shared [3][NN]
   TA* vout;  // shared [3][NN]
   double* red;  // shared 2*512
+  int bc;       // 0 periodic, 1 KUBC (pinned3)
   double Fb[9];
 };
 
 // ---------------------------------------------------------------- FP64 residual
-template <typename TA>
+template <typename TA, int LAW>
 __device__ __noinline__ void residual3(const Ctx3<TA>& c, const double* w, double (&Psum)[9], double& bad) {
   const int n = c.g.n;
   const double ih = (double)n, cw = 0.125 / (ih * ih);  // wq / h = h^2 / 8
@@ -364,14 +438,26 @@ __device__ __noinline__ void residual3(const Ctx3<TA>& c, const double* w, doubl
       nat_grad(u, s, t, r, G);
 #pragma unroll
       for (int k = 0; k < 9; ++k) F[k] = c.Fb[k] + ih * G[k];
-      const NH3<double> m = nh3_eval(F, lam, mu);
-      bad += m.J > 0.0 ? 0.0 : 1.0;
       double P[9];
+      if constexpr (LAW == kLawNH) {
+        const NH3<double> m = nh3_eval(F, lam, mu);
+        bad += m.J > 0.0 ? 0.0 : 1.0;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        P[k] = mu * F[k] + m.hb * m.Fit[k];
-        Psum[k] += P[k];
+        for (int k = 0; k < 9; ++k) P[k] = mu * F[k] + m.hb * m.Fit[k];
+      } else {
+        const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                         F[2] * (F[3] * F[7] - F[4] * F[6]);
+        bad += J > 0.0 ? 0.0 : 1.0;
+        double S6[6];
+        svk3_S(F, lam, mu, S6);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int J2 = 0; J2 < 3; ++J2)
+            P[3 * i + J2] = F[3 * i] * sym6(S6, 0, J2) + F[3 * i + 1] * sym6(S6, 1, J2) + F[3 * i + 2] * sym6(S6, 2, J2);
       }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Psum[k] += P[k];
       nat_scatter(P, cw, s, t, r, y);
     }
 #pragma unroll
@@ -382,7 +468,7 @@ __device__ __noinline__ void residual3(const Ctx3<TA>& c, const double* w, doubl
 }
 
 // sum over this thread's elements of psi at the Gauss points (FP64; Eq. NH-free-energy)
-template <typename TA>
+template <typename TA, int LAW>
 __device__ __noinline__ double energy3(const Ctx3<TA>& c, const double* w) {
   const int n = c.g.n;
   const double ih = (double)n;
@@ -403,12 +489,26 @@ __device__ __noinline__ double energy3(const Ctx3<TA>& c, const double* w) {
       nat_grad(u, s, t, r, G);
 #pragma unroll
       for (int k = 0; k < 9; ++k) F[k] = c.Fb[k] + ih * G[k];
-      const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
-                       F[2] * (F[3] * F[7] - F[4] * F[6]);
-      double trC = 0.0;
+      if constexpr (LAW == kLawNH) {
+        const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                         F[2] * (F[3] * F[7] - F[4] * F[6]);
+        double trC = 0.0;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) trC += F[k] * F[k];
-      acc += 0.25 * lam * (J * J - 1.0) - (0.5 * lam + mu) * log(J) + 0.5 * mu * (trC - 3.0);
+        for (int k = 0; k < 9; ++k) trC += F[k] * F[k];
+        acc += 0.25 * lam * (J * J - 1.0) - (0.5 * lam + mu) * log(J) + 0.5 * mu * (trC - 3.0);
+      } else {  // lam/2 (tr E)^2 + mu E:E, E = (F^T F - I)/2
+        double E[9];
+#pragma unroll
+        for (int I = 0; I < 3; ++I)
+#pragma unroll
+          for (int J2 = 0; J2 < 3; ++J2)
+            E[3 * I + J2] = 0.5 * (F[I] * F[J2] + F[3 + I] * F[3 + J2] + F[6 + I] * F[6 + J2] - (I == J2 ? 1.0 : 0.0));
+        const double trE = E[0] + E[4] + E[8];
+        double ee = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ee += E[k] * E[k];
+        acc += 0.5 * lam * trE * trE + mu * ee;
+      }
     }
   }
   return acc;
@@ -431,7 +531,7 @@ __device__ __forceinline__ void gather_R(const Ctx3<TA>& c, int v, double (&R)[3
 // ------------------------------------------------------- tangent data (TA)
 // Gauss-point data and nodal diagonal blocks (accumulated in shared memory vin|vout as
 // [6][NN]); optional FP64 accumulation of <A> (45 symmetric entries) for the transfer.
-template <typename TA, bool withA>
+template <typename TA, int LAW, bool withA>
 __device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double* Asum /*[45] per thread, withA only*/) {
   const int n = c.g.n, NN = c.g.NN;
   TA* diag = c.vin;  // [6][NN] spans vin and vout
@@ -460,43 +560,100 @@ __device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double
       nat_grad(u, s, t, r, G);
 #pragma unroll
       for (int k = 0; k < 9; ++k) F[k] = (TA)c.Fb[k] + ih * G[k];
-      const NH3<TA> m = nh3_eval(F, lam, mu);
-      TA qv[12];
+      if constexpr (LAW == kLawNH) {
+        const NH3<TA> m = nh3_eval(F, lam, mu);
+        TA qv[12];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) qv[k] = m.Fit[k];
-      qv[9] = m.hb;
-      qv[10] = m.gm;
-      qv[11] = TA(0);
-      store_qp(c.sc.qpd, c.NE, q, e, qv);
-      // diagonal blocks: K_aa,ik = wq [mu |g_a|^2 d_ik + (gm - hb) v_a,i v_a,k], v_a = Fit g_a
+        for (int k = 0; k < 9; ++k) qv[k] = m.Fit[k];
+        qv[9] = m.hb;
+        qv[10] = m.gm;
+        qv[11] = TA(0);
+        store_qp<12>(c.sc.qpd, c.NE, q, e, qv);
+        // diagonal blocks: K_aa,ik = wq [mu |g_a|^2 d_ik + (gm - hb) v_a,i v_a,k], v_a = Fit g_a
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int ox = a & 1, oy = (a >> 1) & 1, oz = (a >> 2) & 1;
-        const TA gx = ih * (ox ? TA(1) : TA(-1)) * phi(oy, t) * phi(oz, r);
-        const TA gy = ih * (oy ? TA(1) : TA(-1)) * phi(ox, s) * phi(oz, r);
-        const TA gz = ih * (oz ? TA(1) : TA(-1)) * phi(ox, s) * phi(oy, t);
-        const TA v0 = m.Fit[0] * gx + m.Fit[1] * gy + m.Fit[2] * gz;
-        const TA v1 = m.Fit[3] * gx + m.Fit[4] * gy + m.Fit[5] * gz;
-        const TA v2 = m.Fit[6] * gx + m.Fit[7] * gy + m.Fit[8] * gz;
-        const TA mg = wq * mu * (gx * gx + gy * gy + gz * gz), cc = wq * (m.gm - m.hb);
-        D[a][0] += mg + cc * v0 * v0;
-        D[a][1] += cc * v0 * v1;
-        D[a][2] += cc * v0 * v2;
-        D[a][3] += mg + cc * v1 * v1;
-        D[a][4] += cc * v1 * v2;
-        D[a][5] += mg + cc * v2 * v2;
-      }
-      if constexpr (withA) {  // <A>_(iJ)(kL), upper triangle of the 9x9 major-symmetric matrix
-        int idx = 0;
+        for (int a = 0; a < 8; ++a) {
+          const int ox = a & 1, oy = (a >> 1) & 1, oz = (a >> 2) & 1;
+          const TA gx = ih * (ox ? TA(1) : TA(-1)) * phi(oy, t) * phi(oz, r);
+          const TA gy = ih * (oy ? TA(1) : TA(-1)) * phi(ox, s) * phi(oz, r);
+          const TA gz = ih * (oz ? TA(1) : TA(-1)) * phi(ox, s) * phi(oy, t);
+          const TA v0 = m.Fit[0] * gx + m.Fit[1] * gy + m.Fit[2] * gz;
+          const TA v1 = m.Fit[3] * gx + m.Fit[4] * gy + m.Fit[5] * gz;
+          const TA v2 = m.Fit[6] * gx + m.Fit[7] * gy + m.Fit[8] * gz;
+          const TA mg = wq * mu * (gx * gx + gy * gy + gz * gz), cc = wq * (m.gm - m.hb);
+          D[a][0] += mg + cc * v0 * v0;
+          D[a][1] += cc * v0 * v1;
+          D[a][2] += cc * v0 * v2;
+          D[a][3] += mg + cc * v1 * v1;
+          D[a][4] += cc * v1 * v2;
+          D[a][5] += mg + cc * v2 * v2;
+        }
+        if constexpr (withA) {  // <A>_(iJ)(kL), upper triangle of the 9x9 major-symmetric matrix
+          int idx = 0;
 #pragma unroll
-        for (int p = 0; p < 9; ++p)
+          for (int p = 0; p < 9; ++p)
 #pragma unroll
-          for (int qq = p; qq < 9; ++qq) {
-            const int i = p / 3, J = p % 3, k = qq / 3, L = qq % 3;
-            TA val = -m.hb * m.Fit[3 * i + L] * m.Fit[3 * k + J] + m.gm * m.Fit[3 * i + J] * m.Fit[3 * k + L];
-            if (i == k && J == L) val += mu;
-            Asum[idx++] += (double)(wq * val);
+            for (int qq = p; qq < 9; ++qq) {
+              const int i = p / 3, J = p % 3, k = qq / 3, L = qq % 3;
+              TA val = -m.hb * m.Fit[3 * i + L] * m.Fit[3 * k + J] + m.gm * m.Fit[3 * i + J] * m.Fit[3 * k + L];
+              if (i == k && J == L) val += mu;
+              Asum[idx++] += (double)(wq * val);
+            }
+        }
+      } else {
+        TA S6[6];
+        svk3_S(F, lam, mu, S6);
+        TA qv[16];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) qv[k] = F[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) qv[9 + k] = S6[k];
+        qv[15] = TA(0);
+        store_qp<16>(c.sc.qpd, c.NE, q, e, qv);
+        TA b6[6];  // b = F F^T (00, 01, 02, 11, 12, 22)
+        {
+          const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+          for (int k = 0; k < 6; ++k)
+            b6[k] = F[3 * I6[k]] * F[3 * J6[k]] + F[3 * I6[k] + 1] * F[3 * J6[k] + 1] + F[3 * I6[k] + 2] * F[3 * J6[k] + 2];
+        }
+        // diagonal blocks: K_aa,ik = wq [d_ik g_a.S.g_a + lam v_a,i v_a,k + mu (|g_a|^2 b_ik + v_a,i v_a,k)],
+        // v_a = F g_a
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int ox = a & 1, oy = (a >> 1) & 1, oz = (a >> 2) & 1;
+          const TA g[3] = {ih * (ox ? TA(1) : TA(-1)) * phi(oy, t) * phi(oz, r),
+                           ih * (oy ? TA(1) : TA(-1)) * phi(ox, s) * phi(oz, r),
+                           ih * (oz ? TA(1) : TA(-1)) * phi(ox, s) * phi(oy, t)};
+          TA v[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) v[i] = F[3 * i] * g[0] + F[3 * i + 1] * g[1] + F[3 * i + 2] * g[2];
+          TA gSg = TA(0);
+#pragma unroll
+          for (int I = 0; I < 3; ++I)
+#pragma unroll
+            for (int J = 0; J < 3; ++J) gSg += g[I] * sym6(S6, I, J) * g[J];
+          const TA gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+          const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            TA val = (lam + mu) * v[I6[k]] * v[J6[k]] + mu * gg * b6[k];
+            if (I6[k] == J6[k]) val += gSg;
+            D[a][k] += wq * val;
           }
+        }
+        if constexpr (withA) {  // A_iJkL = d_ik S_JL + lam F_iJ F_kL + mu b_ik d_JL + mu F_iL F_kJ
+          int idx = 0;
+#pragma unroll
+          for (int p = 0; p < 9; ++p)
+#pragma unroll
+            for (int qq = p; qq < 9; ++qq) {
+              const int i = p / 3, J = p % 3, k = qq / 3, L = qq % 3;
+              TA val = lam * F[3 * i + J] * F[3 * k + L] + mu * F[3 * i + L] * F[3 * k + J];
+              if (i == k) val += sym6(S6, J, L);
+              if (J == L) val += mu * sym6(b6, i, k);
+              Asum[idx++] += (double)(wq * val);
+            }
+        }
       }
     }
 #pragma unroll
@@ -512,7 +669,7 @@ __device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double
     const TA c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
     const TA c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
     const TA det = a00 * c00 + a01 * c01 + a02 * c02;
-    const TA id = v == 0 ? TA(0) : TA(1) / det;
+    const TA id = pinned3(v, n, c.bc) ? TA(0) : TA(1) / det;
     c.sc.mi[v] = c00 * id;
     c.sc.mi[NN + v] = c01 * id;
     c.sc.mi[2 * NN + v] = c02 * id;
@@ -526,7 +683,7 @@ __device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double
 // Kept out of line so the element loop gets its own register allocation (no spills).
 // vout = K vin (mode 0) or vout = L_c: the element operator applied to the constant
 // gradient E_c (mode 1, c = 3k + L).  Pinned node 0 row zeroed.
-template <typename TA>
+template <typename TA, int LAW>
 __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
   const int n = c.g.n, NN = c.g.NN;
   for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.vout[v] = TA(0);
@@ -542,7 +699,8 @@ __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) u[a][i] = c.vin[i * NN + nd[a]];
     }
-    const TA mu = (TA)c.lame[2 * c.phase[e] + 1];
+    const int ph = c.phase[e];
+    const TA mu = (TA)c.lame[2 * ph + 1];
     TA y[8][3];
 #pragma unroll
     for (int a = 0; a < 8; ++a) y[a][0] = y[a][1] = y[a][2] = TA(0);
@@ -559,15 +717,21 @@ __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) dF[k] = k == cidx ? TA(1) : TA(0);
       }
-      TA qv[12];
-      load_qp(c.sc.qpd, c.NE, q, e, qv);
       TA dP[9];
-      tangent_action(qv, qv[9], qv[10], mu, dF, dP);
+      if constexpr (LAW == kLawNH) {
+        TA qv[12];
+        load_qp<12>(c.sc.qpd, c.NE, q, e, qv);
+        tangent_action(qv, qv[9], qv[10], mu, dF, dP);
+      } else {
+        TA qv[16];
+        load_qp<16>(c.sc.qpd, c.NE, q, e, qv);
+        svk_tangent_action(qv, qv + 9, (TA)c.lame[2 * ph], mu, dF, dP);
+      }
       nat_scatter(dP, cw, s, t, r, y);
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      if (nd[a] == 0) continue;
+      if (pinned3(nd[a], n, c.bc)) continue;
 #pragma unroll
       for (int i = 0; i < 3; ++i) atomicAdd(&c.vout[i * NN + nd[a]], y[a][i]);
     }
@@ -591,7 +755,6 @@ __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
 // omega < 2 / lambda_max(D^-1 K).  For Hex8 elasticity lambda_max is about 3.0 (measured on the
 // 8^3 two-sphere RVE), so omega = 0.7 (used in 2D, where lambda_max is about 2.3) is too large
 // here; 0.6 keeps a margin.
-constexpr float kMg3Omega = 0.6f;
 
 __host__ __device__ constexpr int pair8(int a, int b) {  // a <= b
   return a * 8 - (a * (a - 1)) / 2 + (b - a);
@@ -607,7 +770,7 @@ __device__ __forceinline__ TA mg3_kb(const Mg3Level<TA>& L, int E, int a, int b,
 __device__ __forceinline__ int node3(int n, int i, int j, int k) { return i + n * (j + n * k); }
 
 // level 1 element blocks, task (E, a): row block a, b >= a, from the fine Gauss-point data
-template <typename TA>
+template <typename TA, int LAW>
 __device__ __noinline__ void mg3_build_level1(const Ctx3<TA>& c) {
   const Mg3Level<TA> L = c.mg.level(1);
   const int n = c.g.n, nc = L.n;
@@ -625,19 +788,42 @@ __device__ __noinline__ void mg3_build_level1(const Ctx3<TA>& c) {
       const int sx = sub & 1, sy = (sub >> 1) & 1, sz = sub >> 2;
       const int e = node3(n, 2 * I + sx, 2 * J + sy, 2 * K + sz);
       const TA mu = (TA)c.lame[2 * c.phase[e] + 1];
+      const TA lam = (TA)c.lame[2 * c.phase[e]];
 #pragma unroll 1
       for (int q = 0; q < 8; ++q) {
         const TA xi = TA(0.5) * ((TA)sx + (TA)g01(q & 1)), et = TA(0.5) * ((TA)sy + (TA)g01((q >> 1) & 1)),
                  ze = TA(0.5) * ((TA)sz + (TA)g01(q >> 2));
-        TA qv[12];
-        load_qp(c.sc.qpd, c.NE, q, e, qv);
         const TA gax = ihc * (ax ? TA(1) : TA(-1)) * phi(ay, et) * phi(az, ze);
         const TA gay = ihc * (ay ? TA(1) : TA(-1)) * phi(ax, xi) * phi(az, ze);
         const TA gaz = ihc * (az ? TA(1) : TA(-1)) * phi(ax, xi) * phi(ay, et);
+        // neo-Hookean: K = mu d_ik g_a.g_b + gm v_a,i v_b,k - hb v_b,i v_a,k, v = Fit g
+        // St. Venant-Kirchhoff: K = d_ik g_a.S.g_b + lam v_a,i v_b,k + mu ((g_a.g_b) b_ik + v_b,i v_a,k),
+        // v = F g, b = F F^T
+        TA qv[qp_vals<LAW>()];
+        load_qp<qp_vals<LAW>()>(c.sc.qpd, c.NE, q, e, qv);
         TA va[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) va[i] = qv[3 * i] * gax + qv[3 * i + 1] * gay + qv[3 * i + 2] * gaz;
-        const TA hb = wq * qv[9], gm = wq * qv[10], wm = wq * mu;
+        TA c_vv, c_sw, wm;  // coefficients of v_a,i v_b,k and of v_b,i v_a,k, and of d_ik g_a.g_b
+        TA Sa[3] = {TA(0), TA(0), TA(0)}, b6[6];  // SVK: S g_a (weighted) and b = F F^T
+        if constexpr (LAW == kLawNH) {
+          c_vv = wq * qv[10];
+          c_sw = -wq * qv[9];
+          wm = wq * mu;
+        } else {
+          c_vv = wq * lam;
+          c_sw = wq * mu;
+          wm = TA(0);
+          const TA S6[6] = {qv[9], qv[10], qv[11], qv[12], qv[13], qv[14]};
+          const TA ga[3] = {gax, gay, gaz};
+#pragma unroll
+          for (int I = 0; I < 3; ++I) Sa[I] = wq * (sym6(S6, I, 0) * ga[0] + sym6(S6, I, 1) * ga[1] + sym6(S6, I, 2) * ga[2]);
+          const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+          for (int k = 0; k < 6; ++k)
+            b6[k] = wq * mu * (qv[3 * I6[k]] * qv[3 * J6[k]] + qv[3 * I6[k] + 1] * qv[3 * J6[k] + 1] +
+                               qv[3 * I6[k] + 2] * qv[3 * J6[k] + 2]);
+        }
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
           if (b < a) continue;
@@ -648,11 +834,17 @@ __device__ __noinline__ void mg3_build_level1(const Ctx3<TA>& c) {
           TA vb[3];
 #pragma unroll
           for (int i = 0; i < 3; ++i) vb[i] = qv[3 * i] * gbx + qv[3 * i + 1] * gby + qv[3 * i + 2] * gbz;
-          const TA gg = wm * (gax * gbx + gay * gby + gaz * gbz);
+          const TA gab = gax * gbx + gay * gby + gaz * gbz;
+          TA dterm = wm * gab;  // the d_ik part
+          if constexpr (LAW == kLawSVK) dterm = Sa[0] * gbx + Sa[1] * gby + Sa[2] * gbz;
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) acc[b][3 * i + k] += gm * va[i] * vb[k] - hb * vb[i] * va[k] + (i == k ? gg : TA(0));
+            for (int k = 0; k < 3; ++k) {
+              TA val = c_vv * va[i] * vb[k] + c_sw * vb[i] * va[k] + (i == k ? dterm : TA(0));
+              if constexpr (LAW == kLawSVK) val += gab * sym6(b6, i, k);
+              acc[b][3 * i + k] += val;
+            }
         }
       }
     }
@@ -740,7 +932,7 @@ __device__ __noinline__ void mg3_build_diag(const Mg3<TA>& mg, int l) {
     const TA c00 = d[3] * d[5] - d[4] * d[4], c01 = d[2] * d[4] - d[1] * d[5], c02 = d[1] * d[4] - d[2] * d[3];
     const TA c11 = d[0] * d[5] - d[2] * d[2], c12 = d[1] * d[2] - d[0] * d[4], c22 = d[0] * d[3] - d[1] * d[1];
     const TA det = d[0] * c00 + d[1] * c01 + d[2] * c02;
-    const TA id = v == 0 ? TA(0) : TA(1) / det;
+    const TA id = pinned3(v, n, L.bc) ? TA(0) : TA(1) / det;
     L.mi[v] = c00 * id;
     L.mi[L.NN + v] = c01 * id;
     L.mi[2 * L.NN + v] = c02 * id;
@@ -770,11 +962,11 @@ __device__ __noinline__ void mg3_build_coarsest(const Mg3<TA>& mg) {
         for (int kk = 0; kk < 3; ++kk) A[(size_t)row * ld + kk * NN + nb] += mg3_kb<TA>(L, E, a, b, ii, kk);
       }
     }
-    if (v == 0) {
+    if (pinned3(v, n, L.bc)) {  // pinned rows: identity; pinned columns of the other rows: zero
       for (int q = 0; q < D; ++q) A[(size_t)row * ld + q] = q == row ? TA(1) : TA(0);
     } else {
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) A[(size_t)row * ld + kk * NN] = TA(0);
+      for (int q = 0; q < D; ++q)
+        if (pinned3(q % NN, n, L.bc)) A[(size_t)row * ld + q] = TA(0);
     }
   }
   __syncthreads();
@@ -799,9 +991,9 @@ __device__ __noinline__ void mg3_build_coarsest(const Mg3<TA>& mg) {
 }
 
 // After tangent3: all coarse levels of the current tangent.
-template <typename TA>
+template <typename TA, int LAW>
 __device__ void mg3_build(const Ctx3<TA>& c) {
-  mg3_build_level1<TA>(c);
+  mg3_build_level1<TA, LAW>(c);
   for (int l = 1; l < c.mg.levels; ++l) {
     __syncthreads();
     mg3_build_next<TA>(c.mg, l);
@@ -817,7 +1009,7 @@ template <typename TA>
 __device__ __forceinline__ void mg3_apply(const Mg3Level<TA>& L, const TA* z, int v, TA (&y)[3]) {
   const int n = L.n, NN = L.NN, i = v % n, j = (v / n) % n, k = v / (n * n);
   y[0] = y[1] = y[2] = TA(0);
-  if (v == 0) return;
+  if (pinned3(v, n, L.bc)) return;
   for (int a = 0; a < 8; ++a) {
     const int ei = (i - (a & 1) + n) % n, ej = (j - ((a >> 1) & 1) + n) % n, ek = (k - (a >> 2) + n) % n;
     const int E = node3(n, ei, ej, ek);
@@ -851,7 +1043,7 @@ __device__ __forceinline__ void mg3_restrict_smooth(const Mg3<TA>& mg, int l, co
   const int nc = C.n, nf = 2 * nc, NNf = nf * nf * nf;
   const int ci = I % nc, cj = (I / nc) % nc, ck = I / (nc * nc);
   TA r[3] = {TA(0), TA(0), TA(0)};
-  if (I != 0) {
+  if (!pinned3(I, nc, mg.bc)) {
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
@@ -866,7 +1058,7 @@ __device__ __forceinline__ void mg3_restrict_smooth(const Mg3<TA>& mg, int l, co
   for (int d = 0; d < 3; ++d) C.r[d * C.NN + I] = r[d];
   if (l < mg.levels) {
     TA z[3];
-    mg3_smooth<TA>(C.mi, C.NN, I, r, (TA)kMg3Omega, z);
+    mg3_smooth<TA>(C.mi, C.NN, I, r, mg.omega, z);
 #pragma unroll
     for (int d = 0; d < 3; ++d) C.z[d * C.NN + I] = z[d];
   }
@@ -900,7 +1092,7 @@ __device__ __forceinline__ const TA* mg3_result(const Mg3<TA>& mg, int l) {
 template <typename TA>
 __device__ __noinline__ void mg3_coarse_cycle(const Mg3<TA>& mg) {
   const int tid = threadIdx.x;
-  const TA om = (TA)kMg3Omega;
+  const TA om = mg.omega;
   for (int l = 1; l < mg.levels; ++l) {  // descend
     const Mg3Level<TA> v = mg.level(l);
     for (int x = tid; x < v.NN; x += blockDim.x) {
@@ -921,7 +1113,7 @@ __device__ __noinline__ void mg3_coarse_cycle(const Mg3<TA>& mg) {
     for (int row = tid; row < D; row += blockDim.x) {
       TA zz = TA(0);
       for (int q = 0; q < D; ++q) zz += A[(size_t)row * ld + q] * C.r[q];
-      C.z[row] = (row % C.NN == 0) ? TA(0) : zz;
+      C.z[row] = pinned3(row % C.NN, C.n, mg.bc) ? TA(0) : zz;
     }
     __syncthreads();
   }
@@ -959,11 +1151,11 @@ __device__ __forceinline__ T div3(T a, T b) {
 
 // Fine-level part of the V-cycle: vin holds the pre-smoothed omega M^-1 r on entry and the
 // preconditioned residual on return (three fine applies per PCG iteration with the caller's).
-template <typename TA>
+template <typename TA, int LAW>
 __device__ __noinline__ void mg3_vcycle_fine(const Ctx3<TA>& c, const TA* r) {
   const Mg3<TA>& mg = c.mg;
   const int NN = c.g.NN;
-  apply3(c, 0, 0);  // vout = K vin
+  apply3<TA, LAW>(c, 0, 0);  // vout = K vin
   const Mg3Level<TA> L1 = mg.level(1);
   for (int I = threadIdx.x; I < L1.NN; I += blockDim.x) mg3_restrict_smooth<TA>(mg, 1, r, c.vout, I);
   __syncthreads();
@@ -976,12 +1168,12 @@ __device__ __noinline__ void mg3_vcycle_fine(const Ctx3<TA>& c, const TA* r) {
     for (int d = 0; d < 3; ++d) c.vin[d * NN + v] += zp[d];
   }
   __syncthreads();
-  apply3(c, 0, 0);  // vout = K vin
+  apply3<TA, LAW>(c, 0, 0);  // vout = K vin
   for (int v = threadIdx.x; v < NN; v += blockDim.x) {
     TA rr[3], dz[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) rr[d] = r[d * NN + v] - c.vout[d * NN + v];
-    mg3_smooth<TA>(c.sc.mi, NN, v, rr, (TA)kMg3Omega, dz);
+    mg3_smooth<TA>(c.sc.mi, NN, v, rr, mg.omega, dz);
 #pragma unroll
     for (int d = 0; d < 3; ++d) c.vin[d * NN + v] += dz[d];
   }
@@ -989,7 +1181,7 @@ __device__ __noinline__ void mg3_vcycle_fine(const Ctx3<TA>& c, const TA* r) {
 }
 
 // Chronopoulos-Gear PCG for K x = b; b given in sc.r on entry (overwritten), x in sc.x.
-template <typename TA>
+template <typename TA, int LAW>
 __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* status) {
   const int NN = c.g.NN;
   TA* x = c.sc.x;
@@ -998,7 +1190,7 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
   TA* s = c.sc.s;
   const TA* mi = c.sc.mi;
   auto precond_to_vin = [&]() {  // u = M^-1 r -> vin: block-Jacobi, or the multigrid V-cycle
-    const TA om = c.mg.levels ? (TA)kMg3Omega : TA(1);
+    const TA om = c.mg.levels ? c.mg.omega : TA(1);
     for (int v = threadIdx.x; v < NN; v += blockDim.x) {
       const TA r0 = r[v], r1 = r[NN + v], r2 = r[2 * NN + v];
       const TA m00 = mi[v], m01 = mi[NN + v], m02 = mi[2 * NN + v], m11 = mi[3 * NN + v], m12 = mi[4 * NN + v],
@@ -1008,7 +1200,7 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
       c.vin[2 * NN + v] = om * (m02 * r0 + m12 * r1 + m22 * r2);
     }
     __syncthreads();
-    if (c.mg.levels) mg3_vcycle_fine<TA>(c, r);
+    if (c.mg.levels) mg3_vcycle_fine<TA, LAW>(c, r);
   };
   // inner products: per thread and per warp in TA, over the block in FP64 (block_dot2_fp64); the
   // stopping test compares the FP64 sums, the step scalars are formed in TA from them
@@ -1023,7 +1215,7 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
   for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) x[v] = TA(0);
   *status = kStatusOk;
   precond_to_vin();
-  apply3(c, 0, 0);
+  apply3<TA, LAW>(c, 0, 0);
   double gd, dd;
   dots(gd, dd);
   TA gamma = (TA)gd, delta = (TA)dd;
@@ -1063,7 +1255,7 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
     }
     __syncthreads();
     precond_to_vin();
-    apply3(c, 0, 0);
+    apply3<TA, LAW>(c, 0, 0);
     double gnd, dnd;
     dots(gnd, dnd);
     const TA gn = (TA)gnd, dn = (TA)dnd;
@@ -1087,7 +1279,7 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
   return it;
 }
 
-template <typename TA>
+template <typename TA, int LAW>
 __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, unsigned char* gscr) {
   const int rv = a.qp_rve[qp];
   const int n = a.rve_n[rv];
@@ -1106,6 +1298,9 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
   c.sc = scratch3_layout<TA>(gscr, NN);
   c.mg.levels = a.mg ? mg3_levels(n) : 0;
   c.mg.n = n;
+  c.mg.bc = a.bc;
+  c.mg.omega = (TA)a.mg_omega;
+  c.bc = a.bc;
   c.mg.base = c.sc.mg;
   if (threadIdx.x < 2 * kMaxPhase) lame_s[threadIdx.x] = a.rve_lame[(size_t)rv * 2 * kMaxPhase + threadIdx.x];
 #pragma unroll
@@ -1113,7 +1308,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
   const double* w_in = a.w_in + a.qp_w_off[qp];
   double* w = a.w_out + a.qp_w_off[qp];
   // the current fluctuation is kept in w_out (FP64, global); node 0 pinned to zero
-  for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) w[v] = v < 3 ? 0.0 : w_in[v];
+  for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) w[v] = pinned3(v / 3, n, a.bc) ? 0.0 : w_in[v];
   __syncthreads();
 
   // Load continuation on failure: a Newton solve that ends in J <= 0, a non-finite residual or a
@@ -1129,13 +1324,13 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       double bad = 0.0;
 #pragma unroll
       for (int k = 0; k < 9; ++k) Psum[k] = 0.0;
-      residual3(c, w, Psum, bad);
+      residual3<TA, LAW>(c, w, Psum, bad);
       __syncthreads();
       double rr = 0.0;
       for (int v = threadIdx.x; v < NN; v += blockDim.x) {
         double R[3];
         gather_R(c, v, R);
-        if (v == 0) R[0] = R[1] = R[2] = 0.0;
+        if (pinned3(v, n, a.bc)) R[0] = R[1] = R[2] = 0.0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           rr += R[d] * R[d];
@@ -1151,7 +1346,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
         ++nhalf;
         step *= 0.5;
         for (int v = threadIdx.x; v < NN; v += blockDim.x) {
-          if (v == 0) continue;
+          if (pinned3(v, n, a.bc)) continue;
 #pragma unroll
           for (int d = 0; d < 3; ++d) w[3 * v + d] -= step * (double)c.sc.x[d * NN + v];
         }
@@ -1174,7 +1369,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
         status = kStatusNewtonCap;
         break;
       }
-      tangent3<TA, false>(c, w, nullptr);
+      tangent3<TA, LAW, false>(c, w, nullptr);
       // The coarse levels are built on the first Newton iteration of a solve (or continuation
       // stage) and reused by the later ones, with the current fine operator, smoother and
       // residual.  The V-cycle stays symmetric; it stays positive definite as long as the reused
@@ -1184,18 +1379,18 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       // levels is run again once with levels rebuilt at the current tangent (its right-hand side
       // is kept in the transfer area, unused during Newton).  The tangent transfer always
       // rebuilds them at the converged state.
-      const bool reused = c.mg.levels && it > 0;
-      if (c.mg.levels && it == 0) mg3_build<TA>(c);
+      const bool reused = c.mg.levels && it > 0 && a.mg_reuse;
+      if (c.mg.levels && !reused) mg3_build<TA, LAW>(c);
       if (reused)
         for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.L[v] = c.sc.r[v];
       int pst = kStatusOk;
-      cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
+      cg_total += pcg3<TA, LAW>(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
       if (reused && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap)) {
-        mg3_build<TA>(c);
+        mg3_build<TA, LAW>(c);
         for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.r[v] = c.sc.L[v];
         __syncthreads();
         pst = kStatusOk;
-        cg_total += pcg3(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
+        cg_total += pcg3<TA, LAW>(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
       }
       if (pst == kStatusPcgBreakdown) {
         status = kStatusPcgBreakdown;
@@ -1204,7 +1399,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       step = 1.0;
       nhalf = 0;
       for (int v = threadIdx.x; v < NN; v += blockDim.x) {
-        if (v == 0) continue;
+        if (pinned3(v, n, a.bc)) continue;
 #pragma unroll
         for (int d = 0; d < 3; ++d) w[3 * v + d] += (double)c.sc.x[d * NN + v];
       }
@@ -1234,7 +1429,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
 #pragma unroll
   for (int k = 0; k < 9; ++k) Pv[k] = Psum[k];
   const bool want_W = usable && (a.flags & kFlagEnergy) && a.W != nullptr;
-  Pv[9] = want_W ? energy3(c, w) : 0.0;
+  Pv[9] = want_W ? energy3<TA, LAW>(c, w) : 0.0;
   block_sum_n<double>(Pv, 10, c.red);
   if (threadIdx.x == 0)
     for (int k = 0; k < 10; ++k) misc[k] = Pv[k];
@@ -1245,13 +1440,13 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
     double As[45];
 #pragma unroll
     for (int k = 0; k < 45; ++k) As[k] = 0.0;
-    tangent3<TA, true>(c, w, As);
-    if (c.mg.levels) mg3_build<TA>(c);
+    tangent3<TA, LAW, true>(c, w, As);
+    if (c.mg.levels) mg3_build<TA, LAW>(c);
     // <A>: 45 FP64 sums in three reductions of 15
     for (int part = 0; part < 3; ++part) block_sum_n<double>(As + 15 * part, 15, c.red);
     // right-hand sides L_c (c = 3k + L) stored [c][3][NN]
     for (int cc = 0; cc < 9; ++cc) {
-      apply3(c, 1, cc);
+      apply3<TA, LAW>(c, 1, cc);
       for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.L[(size_t)cc * 3 * NN + v] = c.vout[v];
     }
     __syncthreads();
@@ -1261,7 +1456,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.r[v] = -c.sc.L[(size_t)cp * 3 * NN + v];
       __syncthreads();
       int pst = kStatusOk;
-      const int ci = pcg3(c, (TA)a.cond_rtol, a.max_cond_cg, false, &pst);
+      const int ci = pcg3<TA, LAW>(c, (TA)a.cond_rtol, a.max_cond_cg, false, &pst);
       cond_total += ci;
       cond_max = ci > cond_max ? ci : cond_max;
       if (pst != kStatusOk && status == kStatusOk) status = pst;
@@ -1305,7 +1500,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
   __syncthreads();
 }
 
-template <typename TA>
+template <typename TA, int LAW>
 __global__ void __launch_bounds__(kThreads3D, 1) rve3d_kernel(const Rve2dArgs a) {
   extern __shared__ __align__(16) unsigned char smem3[];
   __shared__ int s_item;
@@ -1316,7 +1511,7 @@ __global__ void __launch_bounds__(kThreads3D, 1) rve3d_kernel(const Rve2dArgs a)
     const int item = s_item;
     __syncthreads();
     if (item >= (a.n_dev ? *a.n_dev : a.n_qp)) break;
-    solve_item_3d<TA>(a, a.order[item], smem3, gscr);
+    solve_item_3d<TA, LAW>(a, a.order[item], smem3, gscr);
   }
 }
 
@@ -1330,19 +1525,22 @@ size_t rve3d_scratch_bytes(int nn_max, bool mixed, int n_blocks) {
   return (mixed ? scratch3_bytes<float>(nn_max) : scratch3_bytes<double>(nn_max)) * (size_t)n_blocks;
 }
 
+template <typename TA, int LAW>
+cudaError_t rve3d_launch_instance(const Rve2dArgs& a, int n_blocks, size_t smem, cudaStream_t stream) {
+  const cudaError_t err =
+      cudaFuncSetAttribute(rve3d_kernel<TA, LAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  rve3d_kernel<TA, LAW><<<n_blocks, kThreads3D, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t rve3d_launch(const Rve2dArgs& a, bool mixed, int n_blocks, cudaStream_t stream) {
   const size_t smem = rve3d_smem_bytes(a.nn_max, mixed);
-  cudaError_t err;
-  if (mixed) {
-    err = cudaFuncSetAttribute(rve3d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    rve3d_kernel<float><<<n_blocks, kThreads3D, smem, stream>>>(a);
-  } else {
-    err = cudaFuncSetAttribute(rve3d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    rve3d_kernel<double><<<n_blocks, kThreads3D, smem, stream>>>(a);
-  }
-  return cudaGetLastError();
+  if (mixed)
+    return a.law == kLawSVK ? rve3d_launch_instance<float, kLawSVK>(a, n_blocks, smem, stream)
+                            : rve3d_launch_instance<float, kLawNH>(a, n_blocks, smem, stream);
+  return a.law == kLawSVK ? rve3d_launch_instance<double, kLawSVK>(a, n_blocks, smem, stream)
+                          : rve3d_launch_instance<double, kLawNH>(a, n_blocks, smem, stream);
 }
 
 }  // namespace fehmm

@@ -34,6 +34,10 @@ struct Rve2dArgs {
   const int32_t* n_dev;  // optional: number of work items in device memory (order = a qp list)
   int fixed_n;        // fixed-layout launches only: grid size of every RVE
   int phase_per_qp;   // fixed-layout launches only: 1 = one phase map per qp, 0 = one shared
+  int bc;             // 0 periodic (node 0 pinned), 1 KUBC (nodes on the planes x_c = 0 pinned)
+  int law;            // 0 neo-Hookean, 1 St. Venant-Kirchhoff
+  float mg_omega;     // smoother damping of the multigrid V-cycle
+  int mg_reuse;       // 3D: reuse the coarse levels over the Newton iterations of a solve
 };
 
 size_t rve2d_smem_bytes(int nn_max, bool mixed);
@@ -83,6 +87,8 @@ cudaError_t macro_qp_F_launch(const MacroArgs& m, cudaStream_t stream);
 cudaError_t macro_dirichlet_launch(double* u, double* du, int n, const int32_t* dofs, const double* vals, int n_fixed,
                                    double scale, cudaStream_t stream);
 cudaError_t macro_update_launch(double* u, const double* du, int n, cudaStream_t stream);
+cudaError_t macro_spmv_launch(const int32_t* rowptr, const int32_t* col, const double* K, const double* x,
+                              double scale, double* y, int n, cudaStream_t stream);
 cudaError_t macro_assemble_launch(const MacroArgs& m, cudaStream_t stream, int* launches);
 
 }  // namespace fehmm

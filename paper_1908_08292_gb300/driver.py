@@ -30,7 +30,7 @@ from . import SOLVE_FROM_COMMITTED, Context, FehmmError
 
 class LoadStepDriver:
     def __init__(self, problem, precision=None, scheme="nested", graphs=False, macro_rtol=1e-10, macro_atol=1e-13,
-                 max_macro=40, solve_rtol=1e-12, shard=None, **options):
+                 max_macro=40, solve_rtol=1e-12, shard=None, predictor=False, **options):
         import torch
 
         if scheme not in ("nested", "alternating"):
@@ -64,6 +64,11 @@ class LoadStepDriver:
         self.f = torch.zeros(n_rows, dtype=f64, device=dev)
         self.K = torch.zeros(nnz, dtype=f64, device=dev)
         self.info = torch.zeros(3, dtype=f64, device=dev)
+        # tangent predictor of a load step (predictor=True): the Dirichlet increment's load on the
+        # last converged tangent, g = K d, and the correction K_ff delta = -g_f
+        self.predictor = predictor
+        self.g = torch.zeros(n_rows, dtype=f64, device=dev)
+        self.K_valid = False
         # data-parallel ranks (dist.Shard): this rank solves only its points' RVEs, the partial
         # macro systems are summed over ranks, rank 0 solves and broadcasts du and the CG info
         self.shard = shard
@@ -109,11 +114,7 @@ class LoadStepDriver:
         if self.shard is not None:
             self.shard.reduce_system(self.f, self.K)
         if solve:
-            if self.shard is None or self.shard.rank == 0:
-                c.macro_solve(self.K, self.f, self.du, self.info, rtol=self.solve_rtol)
-            if self.shard is not None:
-                self.shard.share_correction(self.du)
-                self.shard.share_correction(self.info)
+            self._solve(self.f)
 
     def _run(self, first):
         import torch
@@ -132,6 +133,47 @@ class LoadStepDriver:
             self._g[key] = g
         self._g[key].replay()
 
+    def _solve(self, f):
+        """du = -K_ff^-1 f_f on rank 0, shared with every rank (with the CG info)."""
+        if self.shard is None or self.shard.rank == 0:
+            self.ctx.macro_solve(self.K, f, self.du, self.info, rtol=self.solve_rtol)
+        if self.shard is not None:
+            self.shard.share_correction(self.du)
+            self.shard.share_correction(self.info)
+
+    def _predict(self, new_scale):
+        """Tangent predictor: with the tangent K of the last converged state (one RVE pass at the
+        current state first if there is none yet), the Dirichlet increment d = (new_scale - scale)
+        u_hat and the interior correction delta with K_ff delta = -(K d)_f; the first macro
+        iteration then starts from u + d + delta instead of concentrating d in the boundary
+        elements.  Returns the number of RVE passes it ran (0 or 1)."""
+        c = self.ctx
+        passes = 0
+        if not self.K_valid:
+            c.macro_qp_F(self.u, self.F)
+            self._constitutive(True)
+            c.macro_assemble(self.P, self.A, self.f, self.K)
+            if self.shard is not None:
+                self.shard.reduce_system(self.f, self.K)
+            passes = 1
+        c.macro_dirichlet_load(self.K, new_scale - self.scale, self.g)
+        self._solve(self.g)
+        c.macro_apply_dirichlet(self.u, None, new_scale)  # u[D] = new values; du keeps delta
+        return passes
+
+    def state(self):
+        """Copy of the load-step state (macro u, committed fluctuations, last tangent) to repeat a step."""
+        return (self.u.clone(), self.ctx.fluctuations(committed=True).clone(), self.K.clone(), self.K_valid,
+                self.scale)
+
+    def restore(self, st):
+        u, w, K, kv, scale = st
+        self.u.copy_(u)
+        self.ctx.fluctuations(committed=True).copy_(w)
+        self.ctx.rollback()
+        self.K.copy_(K)
+        self.K_valid, self.scale = kv, scale
+
     # --------------------------------------------------------------- load step
     def load_step(self, k, commit=True):
         """Run load step k (load factor k / n_steps); returns a record of the iterations.  With
@@ -139,8 +181,13 @@ class LoadStepDriver:
         previous step is kept, so the step can be repeated after restoring u and a rollback)."""
         import torch
         t0 = time.perf_counter()
-        self.scale = k / self.p.n_steps
-        self.ctx.macro_apply_dirichlet(self.u, self.du, self.scale)
+        new_scale = k / self.p.n_steps
+        extra = 0
+        if self.predictor:
+            extra = self._predict(new_scale)
+        else:
+            self.ctx.macro_apply_dirichlet(self.u, self.du, new_scale)
+        self.scale = new_scale
         hist, cg_its, micro = [], [], []
         f0 = None
         converged = False
@@ -163,11 +210,12 @@ class LoadStepDriver:
         if self.scheme == "alternating":  # final micro iteration at the converged u (Sec. 5.2)
             self._iteration(first=False, solve=False)
             micro.append(int(self.it[:, 0].sum().item()))
+        self.K_valid = True  # the last pass assembled the tangent at the converged state
         if commit:
             self.ctx.commit()
         torch.cuda.synchronize()
         return {"step": k, "macro_iters": len(hist) - 1, "macro_hist": hist, "macro_cg": cg_its,
-                "micro_newton": micro, "rve_passes": len(micro), "converged": converged,
+                "micro_newton": micro, "rve_passes": len(micro) + extra, "converged": converged,
                 "seconds": time.perf_counter() - t0}
 
     def run(self, steps=None):

@@ -115,6 +115,31 @@ def test_config1_load_steps_match_oracle(scheme):
         drv.close()
 
 
+def test_config1_tangent_predictor_matches_oracle():
+    """Load steps that start from the tangent predictor (the Dirichlet increment's load on the
+    last converged tangent and the interior correction it implies) against the oracle's driver
+    with the same predictor: same macro iterations, same displacements and stresses."""
+    from paper_1908_08292_gb300.driver import LoadStepDriver
+
+    p = synth.config1()
+    steps = 4
+    ref, mesh = odriver.run(p, scheme="nested", steps_to_run=steps, micro_rtol=1e-12, predictor=True)
+    drv = LoadStepDriver(p, precision="fp64", scheme="nested", newton_rtol=1e-12, newton_atol=1e-15, cg_rtol=1e-9,
+                         cond_rtol=1e-11, predictor=True)
+    try:
+        for k in range(1, steps + 1):
+            rec = drv.load_step(k)
+            assert rec["converged"]
+            u = drv.u.cpu().numpy()
+            P = drv.P.cpu().numpy().reshape(-1, 2, 2)
+            r = ref[k - 1]
+            assert np.abs(u - r["u"]).max() < 1e-9 * np.abs(r["u"]).max()
+            assert np.abs(P - r["P"]).max() < 1e-9 * np.abs(r["P"]).max()
+            assert rec["macro_iters"] == r["macro_iters"]
+    finally:
+        drv.close()
+
+
 def test_graph_replay_equals_eager():
     from paper_1908_08292_gb300.driver import LoadStepDriver
 
