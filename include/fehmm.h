@@ -299,6 +299,10 @@ int fehmm_mlp_loss_grad(fehmm_mlp* mlp, const float* x, const float* ty, const f
 int fehmm_mlp_adamw(fehmm_mlp* mlp, float lr, float beta1, float beta2, float eps, float weight_decay,
                     void* stream);
 long long fehmm_mlp_launch_count(const fehmm_mlp* mlp);
+/* Device view of the gradient that fehmm_mlp_loss_grad wrote and fehmm_mlp_adamw reads (FP32,
+ * packed like the parameters; owned by the MLP).  Data-parallel training over ranks sums it over
+ * the ranks between the two calls (each rank's loss weighted by 1/(global batch)). */
+int fehmm_mlp_grad_buffer(fehmm_mlp* mlp, float** dev_ptr, int* n_params);
 
 typedef struct {
   double lam0, mu0;  /* Lame constants of the neo-Hookean base energy */
@@ -321,6 +325,13 @@ typedef struct {
 int fehmm_surrogate_eval(fehmm_mlp* mlp, const fehmm_surrogate_params* sp, const double* F, int n,
                          double* P, double* A, double* W, int32_t* inside, float* work, void* stream);
 size_t fehmm_surrogate_work_floats(int n);
+
+/* Persistence of a trained surrogate (host file path): the packed FP32 network parameters and
+ * every field of fehmm_surrogate_params, in a small binary file with a magic and a format
+ * version.  load sets the network's parameters (resetting its optimiser state) and *sp.  An
+ * unreadable, foreign or truncated file returns FEHMM_ERR_ARG and changes nothing. */
+int fehmm_surrogate_save(fehmm_mlp* mlp, const fehmm_surrogate_params* sp, const char* path);
+int fehmm_surrogate_load(fehmm_mlp* mlp, fehmm_surrogate_params* sp, const char* path);
 
 /* Training data of the surrogate from n full RVE solves at F = U (device F [n][9], their
  * homogenised P [n][9] and W [n]): features x [n][6], value targets ty [n] and input-gradient

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <string.h>
 
 #include <new>
 #include <vector>
@@ -645,5 +647,59 @@ int fehmm_mlp_adamw(fehmm_mlp* m, float lr, float beta1, float beta2, float eps,
 }
 
 long long fehmm_mlp_launch_count(const fehmm_mlp* m) { return m ? m->launches : -1; }
+
+int fehmm_mlp_grad_buffer(fehmm_mlp* m, float** dev_ptr, int* n) {
+  if (!m || !dev_ptr) return FEHMM_ERR_ARG;
+  *dev_ptr = m->G;
+  if (n) *n = N_PARAMS;
+  return FEHMM_OK;
+}
+
+// Surrogate file: magic, format version, parameter count, the packed FP32 parameters, then the
+// fehmm_surrogate_params fields as little-endian doubles in declaration order (every double of
+// the struct is written, so a load reproduces the evaluation exactly).
+namespace {
+constexpr char kMagic[8] = {'F', 'E', 'H', 'M', 'M', 'S', 'U', 'R'};
+constexpr int32_t kFormat = 1;
+constexpr size_t kSpDoubles = sizeof(fehmm_surrogate_params) / sizeof(double);
+static_assert(sizeof(fehmm_surrogate_params) == kSpDoubles * sizeof(double), "surrogate params are all doubles");
+}  // namespace
+
+int fehmm_surrogate_save(fehmm_mlp* m, const fehmm_surrogate_params* sp, const char* path) {
+  if (!m || !sp || !path) return FEHMM_ERR_ARG;
+  std::vector<float> params(N_PARAMS);
+  const int rc = fehmm_mlp_get_params(m, params.data(), nullptr);
+  if (rc != FEHMM_OK) return rc;
+  FILE* f = fopen(path, "wb");
+  if (!f) return FEHMM_ERR_ARG;
+  const int32_t np = N_PARAMS, nsp = (int32_t)kSpDoubles;
+  bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(&kFormat, sizeof(kFormat), 1, f) == 1 &&
+            fwrite(&np, sizeof(np), 1, f) == 1 && fwrite(&nsp, sizeof(nsp), 1, f) == 1 &&
+            fwrite(params.data(), sizeof(float), N_PARAMS, f) == (size_t)N_PARAMS &&
+            fwrite(sp, sizeof(double), kSpDoubles, f) == kSpDoubles;
+  ok = (fclose(f) == 0) && ok;
+  return ok ? FEHMM_OK : FEHMM_ERR_ARG;
+}
+
+int fehmm_surrogate_load(fehmm_mlp* m, fehmm_surrogate_params* sp, const char* path) {
+  if (!m || !sp || !path) return FEHMM_ERR_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return FEHMM_ERR_ARG;
+  char magic[8];
+  int32_t fmt = 0, np = 0, nsp = 0;
+  std::vector<float> params(N_PARAMS);
+  fehmm_surrogate_params tmp;
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 && fread(&fmt, sizeof(fmt), 1, f) == 1 &&
+            fmt == kFormat && fread(&np, sizeof(np), 1, f) == 1 && np == N_PARAMS &&
+            fread(&nsp, sizeof(nsp), 1, f) == 1 && nsp == (int32_t)kSpDoubles &&
+            fread(params.data(), sizeof(float), N_PARAMS, f) == (size_t)N_PARAMS &&
+            fread(&tmp, sizeof(double), kSpDoubles, f) == kSpDoubles;
+  fclose(f);
+  if (!ok) return FEHMM_ERR_ARG;
+  const int rc = fehmm_mlp_set_params(m, params.data());
+  if (rc != FEHMM_OK) return rc;
+  *sp = tmp;
+  return FEHMM_OK;
+}
 
 }  // extern "C"

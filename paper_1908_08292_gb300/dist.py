@@ -9,6 +9,11 @@ sum over ranks of the residual f and of the CSR tangent values K gives the globa
 single exchange of a macro iteration.  Rank 0 solves the (small) macro system and broadcasts the
 correction, so every rank holds the same macro state by construction.
 
+The surrogate network trains data-parallel the same way: every rank takes its slice of each
+global batch (batch_slice), its loss carries the weight 1/(global batch), so one sum of the
+gradient buffer over the ranks (allreduce_gradient, about 200 KB in FP32) gives every rank the
+full-batch gradient and identical AdamW steps.
+
 Host logic only (partition, qp lists, the collectives on tensors); every arithmetic step of an
 iteration runs in the library's kernels.  The collectives work on CUDA tensors with NCCL and on
 CPU tensors with gloo.
@@ -43,6 +48,21 @@ def partition_elements(cost: np.ndarray, world: int) -> list[tuple[int, int]]:
 def element_cost(rve_dofs_per_qp: np.ndarray, nq: int) -> np.ndarray:
     """Per-element cost = sum of the RVE dofs of its nq points (qp = element * nq + l)."""
     return np.asarray(rve_dofs_per_qp, dtype=np.float64).reshape(-1, nq).sum(axis=1)
+
+
+def batch_slice(s0: int, batch: int, rank: int, world: int) -> tuple[int, int]:
+    """Rows [a, b) of the global batch [s0, s0 + batch) that `rank` of `world` trains on
+    (contiguous, sizes differing by at most one)."""
+    a = s0 + (batch * rank) // world
+    b = s0 + (batch * (rank + 1)) // world
+    return a, b
+
+
+def allreduce_gradient(grad, world: int):
+    """Sum a gradient tensor over the ranks, in place (no-op on one rank)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(grad, op=dist.ReduceOp.SUM)
 
 
 def qp_range_list(e0: int, e1: int, nq: int) -> np.ndarray:

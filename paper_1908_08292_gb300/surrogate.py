@@ -104,6 +104,15 @@ class MLP:
         _check(lib().fehmm_mlp_get_params(self._h, v.ctypes.data, None), "mlp_get_params")
         return v
 
+    def grad_buffer(self):
+        """Device view (torch float32, no copy) of the gradient of the last loss_grad call."""
+        import torch
+
+        from . import _DevArray
+        ptr, n = ctypes.c_void_p(), ctypes.c_int()
+        _check(lib().fehmm_mlp_grad_buffer(self._h, ctypes.byref(ptr), ctypes.byref(n)), "mlp_grad_buffer")
+        return torch.as_tensor(_DevArray(ptr.value, n.value, "<f4"), device="cuda")
+
     def get_grad(self):
         v = np.zeros(n_params(), dtype=np.float32)
         _check(lib().fehmm_mlp_get_params(self._h, None, v.ctypes.data), "mlp_get_params")
@@ -155,6 +164,18 @@ class SurrogateParams(ctypes.Structure):
             self.g0[k] = float(gh[k])
         for k in range(36):
             self.H0[k] = float(0.5 * (Hh[k] + Hh[6 * (k % 6) + k // 6])) if hessian else 0.0
+
+
+def save(mlp: MLP, sp: SurrogateParams, path: str):
+    """Write the trained network and its surrogate parameters to a file."""
+    _check(lib().fehmm_surrogate_save(mlp._h, ctypes.byref(sp), str(path).encode()), "surrogate_save")
+
+
+def load(mlp: MLP, path: str) -> SurrogateParams:
+    """Read a surrogate file into `mlp`; returns its surrogate parameters."""
+    sp = SurrogateParams()
+    _check(lib().fehmm_surrogate_load(mlp._h, ctypes.byref(sp), str(path).encode()), "surrogate_load")
+    return sp
 
 
 def surrogate_eval(mlp: MLP, sp: SurrogateParams, F, P, A, W, inside, work, stream=None):
@@ -286,10 +307,15 @@ def generate(ctx, sp, U, chunk=None, stages=3, drop_failed=True):
     return x, ty, tg, Ps, Ws, bad
 
 
-def train(mlp, x, ty, tg, epochs, batch=4096, lr=2e-3, lr_end=2e-5, weight_decay=0.0, cg_weight=1.0, log=None):
+def train(mlp, x, ty, tg, epochs, batch=4096, lr=2e-3, lr_end=2e-5, weight_decay=0.0, cg_weight=1.0, log=None,
+          rank=0, world=1):
     """AdamW over contiguous batches of i.i.d. samples; cosine learning-rate decay.  Loss weights
-    normalise each term by its target's mean square."""
+    normalise each term by its target's mean square.  With world > 1 (one process per GPU, the
+    same x, ty, tg on every rank) each rank trains on its slice of every global batch and the
+    gradient is summed over the ranks before each AdamW step (dist.allreduce_gradient)."""
     import torch
+
+    from .dist import allreduce_gradient, batch_slice
     N = x.shape[0]
     cy = 1.0 / max(float((ty.double() ** 2).mean().item()), 1e-30) / batch
     cgw = cg_weight / max(float((tg.double() ** 2).sum(1).mean().item()), 1e-30) / batch
@@ -301,7 +327,9 @@ def train(mlp, x, ty, tg, epochs, batch=4096, lr=2e-3, lr_end=2e-5, weight_decay
         for s0 in range(0, N - batch + 1, batch):
             t = k / max(1, steps - 1)
             rate = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * t))
-            mlp.loss_grad(x[s0:s0 + batch], ty[s0:s0 + batch], tg[s0:s0 + batch], cy, cgw, loss)
+            a, b = batch_slice(s0, batch, rank, world)
+            mlp.loss_grad(x[a:b], ty[a:b], tg[a:b], cy, cgw, loss)
+            allreduce_gradient(mlp.grad_buffer() if world > 1 else None, world)
             mlp.adamw(rate, weight_decay=weight_decay)
             k += 1
         hist.append(float(loss.item()))

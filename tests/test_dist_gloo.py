@@ -109,3 +109,54 @@ def test_two_gloo_ranks_reproduce_the_single_process_iteration(tmp_path):
         np.testing.assert_allclose(r[k]["K"], K.toarray().reshape(-1), rtol=0, atol=1e-12)
         np.testing.assert_allclose(r[k]["du"], du, rtol=1e-11, atol=1e-14)
     assert np.array_equal(r[0]["du"], r[1]["du"])  # the broadcast makes the macro state identical
+
+
+def _grad_rank_main(rank, world, port, out_dir):
+    """One data-parallel training step's gradient: this rank's slice of the global batch, the
+    oracle's double-backward gradient standing in for the library's kernels, loss weights
+    1/(global batch), then the sum over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    from oracle import mlp as omlp
+    from paper_1908_08292_gb300.dist import allreduce_gradient, batch_slice
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        params, x, ty, tg, B = _grad_inputs()
+        a, b = batch_slice(0, B, rank, world)
+        G = omlp.param_grad(params, x[a:b], ty[a:b], tg[a:b], 1.0 / B, 0.5 / B)
+        flat = torch.tensor(np.concatenate([np.asarray(G[k]).reshape(-1) for k in sorted(G)]))
+        allreduce_gradient(flat, world)
+        np.save(os.path.join(out_dir, f"grad{rank}.npy"), flat.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def _grad_inputs():
+    from oracle import mlp as omlp
+    params = omlp.init_params(91)
+    B = 37  # odd: the two slices differ in size
+    x = synth.random_field(92, B, 6, 0.8)
+    ty = synth.random_field(93, 1, B, 1.0)[0]
+    tg = synth.random_field(94, B, 6, 1.0)
+    return params, x, ty, tg, B
+
+
+def test_two_gloo_ranks_sum_to_the_full_batch_gradient(tmp_path):
+    """Data-parallel surrogate training: the per-rank gradients of the rank slices, summed by
+    allreduce_gradient, equal the full-batch gradient on every rank."""
+    import torch.multiprocessing as mp
+
+    from oracle import mlp as omlp
+    from paper_1908_08292_gb300.dist import batch_slice
+    world, port = 2, _free_port()
+    mp.spawn(_grad_rank_main, args=(world, port, str(tmp_path)), nprocs=world, join=True)
+    params, x, ty, tg, B = _grad_inputs()
+    G = omlp.param_grad(params, x, ty, tg, 1.0 / B, 0.5 / B)
+    full = np.concatenate([np.asarray(G[k]).reshape(-1) for k in sorted(G)])
+    got = [np.load(os.path.join(tmp_path, f"grad{k}.npy")) for k in range(world)]
+    assert [batch_slice(0, B, r, world) for r in range(world)] == [(0, 18), (18, 37)]
+    for g in got:
+        np.testing.assert_allclose(g, full, rtol=1e-12, atol=1e-14 * np.abs(full).max())
+    assert np.array_equal(got[0], got[1])

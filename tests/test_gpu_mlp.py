@@ -45,6 +45,15 @@ def test_mlp_eval_forward_gradient_hessian():
     assert rel(y.cpu().numpy(), yr) < 4e-3
     assert rel(g.cpu().numpy(), gr) < 4e-3
     assert rel(H.cpu().numpy(), Hr) < 8e-3
+    # per sample (row): a wrong row or a wrong ragged tail tile (rows 256..299 of the 64-row
+    # tiles) cannot hide in a batch norm; each row's error relative to the row's own size,
+    # floored at 10 % of the batch RMS (rows near zero)
+    yg, gg, Hg = y.cpu().numpy(), g.cpu().numpy(), H.cpu().numpy().reshape(B, 36)
+    for got, ref, tol in ((yg[:, None], yr[:, None], 1.5e-2), (gg, gr, 1.5e-2), (Hg, Hr.reshape(B, 36), 3e-2)):
+        floor = 0.1 * np.sqrt((ref ** 2).sum(axis=1).mean())
+        row = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), floor)
+        assert row.max() < tol, (int(row.argmax()), float(row.max()))
+        assert row[256:].max() < tol  # the ragged tail tile
     # and close to the unquantised FP64 network (BF16 error budget)
     y64, g64, H64 = omlp.input_hessian(p, x)
     assert rel(y.cpu().numpy(), y64) < 3e-2 and rel(g.cpu().numpy(), g64) < 3e-2
@@ -74,6 +83,31 @@ def test_mlp_loss_parameter_gradient():
     assert abs(loss.item() - Lr) < 2e-3 * Lr
     for k in Gr:
         assert rel(G[k], Gr[k]) < 2e-2, (k, rel(G[k], Gr[k]))
+        # element by element, against the tensor's largest entry: a wrong index or sign in one
+        # bias row or one input column cannot hide under the tensor norm
+        err = np.abs(np.asarray(G[k]) - np.asarray(Gr[k])).max() / np.abs(Gr[k]).max()
+        assert err < 3e-2, (k, err)
+
+    # central finite differences of the GPU loss itself for FP32 parameters (the biases, which
+    # the kernels keep in FP32, so a perturbation is not lost to bfloat16 rounding)
+    def gpu_loss(params):
+        m.set_params(params)
+        m.loss_grad(torch.tensor(x, dtype=torch.float32, device=dev),
+                    torch.tensor(ty, dtype=torch.float32, device=dev),
+                    torch.tensor(tg, dtype=torch.float32, device=dev), cy, cg, loss)
+        torch.cuda.synchronize()
+        return float(loss.item())
+
+    rng = np.random.default_rng(5)
+    for k, idx in [("b1", int(rng.integers(128))), ("b2", int(rng.integers(128))), ("b4", int(rng.integers(128))),
+                   ("b5", 0)]:
+        h = 2e-2
+        pp, pm = {q: v.copy() for q, v in p.items()}, {q: v.copy() for q, v in p.items()}
+        pp[k].reshape(-1)[idx] += h
+        pm[k].reshape(-1)[idx] -= h
+        fd = (gpu_loss(pp) - gpu_loss(pm)) / (2 * h)
+        gk = float(np.asarray(G[k]).reshape(-1)[idx])
+        assert abs(fd - gk) < 3e-2 * abs(gk) + 2e-3 * np.abs(G[k]).max(), (k, idx, fd, gk)
     m.close()
 
 
@@ -117,6 +151,15 @@ def test_surrogate_eval_and_trust_region():
     assert np.linalg.norm(W.cpu().numpy() - Wr) < 8e-3 * np.linalg.norm(Wr - Wb)
     assert np.linalg.norm(P.cpu().numpy() - Pr.reshape(n, 9)) < 8e-3 * np.linalg.norm((Pr - Pb).reshape(n, 9))
     assert np.linalg.norm(A.cpu().numpy() - Ar.reshape(n, 81)) < 1.6e-2 * np.linalg.norm((Ar - Ab).reshape(n, 81))
+    # per point: each point's error against the size of its own network part (floored at 10 % of
+    # the batch RMS), so that one wrong point cannot hide in the batch norm
+    for got, ref, base, tol in ((W.cpu().numpy()[:, None], Wr[:, None], Wb[:, None], 2e-2),
+                                (P.cpu().numpy(), Pr.reshape(n, 9), Pb.reshape(n, 9), 2e-2),
+                                (A.cpu().numpy(), Ar.reshape(n, 81), Ab.reshape(n, 81), 4e-2)):
+        netpart = np.linalg.norm(ref - base, axis=1)
+        floor = 0.1 * np.sqrt((netpart ** 2).mean())
+        row = np.linalg.norm(got - ref, axis=1) / np.maximum(netpart, floor)
+        assert row.max() < tol, (int(row.argmax()), float(row.max()))
     # with a zero network (and no origin shift) the surrogate is exactly the base law
     sp.y0 = 0.0
     for k in range(6):
@@ -155,3 +198,46 @@ def test_training_reduces_sobolev_loss():
             hist.append(loss.item())
     assert hist[-1] < 0.05 * hist[0], hist
     m.close()
+
+
+def test_surrogate_save_and_load_round_trip(tmp_path):
+    """A saved surrogate (network + surrogate parameters) loads into a fresh network that
+    evaluates bit-identically; a foreign or truncated file is rejected without changes."""
+    import torch
+
+    from paper_1908_08292_gb300 import FehmmError
+    from paper_1908_08292_gb300 import surrogate as su
+    p = net(81)
+    n = 64
+    F = torch.tensor(synth.random_F(82, n, 3, 0.2).reshape(n, 9), device="cuda")
+    m = su.MLP(n)
+    m.set_params(p)
+    sp = su.SurrogateParams(1.2, 0.8, 0.35, 0.02, 0.3)
+    sp.set_Ca(synth.random_field(83, 6, 6, 0.05))
+    sp.set_origin(m)
+    path = str(tmp_path / "sur.bin")
+    su.save(m, sp, path)
+    m2 = su.MLP(n)
+    sp2 = su.load(m2, path)
+    assert bytes(sp2) == bytes(sp)
+    assert np.array_equal(m2.get_params(), m.get_params())
+
+    def run(mm, s):
+        P = torch.zeros(n, 9, dtype=torch.float64, device="cuda")
+        A = torch.zeros(n, 81, dtype=torch.float64, device="cuda")
+        W = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ins = torch.zeros(n, dtype=torch.int32, device="cuda")
+        work = torch.zeros(su.work_floats(n), dtype=torch.float32, device="cuda")
+        su.surrogate_eval(mm, s, F, P, A, W, ins, work)
+        torch.cuda.synchronize()
+        return P.cpu().numpy(), A.cpu().numpy(), W.cpu().numpy()
+
+    for a, b in zip(run(m, sp), run(m2, sp2)):
+        assert np.array_equal(a, b)
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(open(path, "rb").read()[:100])
+    with pytest.raises(FehmmError):
+        su.load(m2, str(bad))
+    assert np.array_equal(m2.get_params(), m.get_params())
+    m.close()
+    m2.close()
