@@ -339,6 +339,33 @@ int fehmm_surrogate_load(fehmm_mlp* mlp, fehmm_surrogate_params* sp, const char*
 int fehmm_surrogate_targets(const fehmm_surrogate_params* sp, const double* F, const double* P, const double* W,
                             int n, float* x, float* ty, float* tg, void* stream);
 
+/*
+ * Autotuner of the solver settings (project-written; the paper has no counterpart).  Times the
+ * batched RVE solve (fehmm_rve_solve_list from the committed fluctuations, at the deformation
+ * gradients F, device [n_qp][d*d]) on an evenly strided sample of n_sample bound points (<= 0:
+ * two per SM) for every candidate setting -- preconditioner (multigrid | block-Jacobi), smoother
+ * damping mg_omega (four values below the element type's positive-definiteness bound), 3D
+ * coarse-level reuse, and the Newton-correction PCG tolerance (cg_rtol x {1, 10, 0.1}) -- and
+ * keeps the fastest whose sample solves all converge; the tolerances the solves meet do not
+ * change.  The choice is written into the context's options and, when cache_path (host text
+ * file, may be NULL) is given, appended to it under a key of dimension, precision, law,
+ * coupling, the grid sizes bound and the device name; a later call with a matching key applies
+ * the cached choice without timing.  The current fluctuations are restored after the trials.
+ * best (host, may be NULL) receives the choice.  Allocates temporary device memory; returns
+ * FEHMM_ERR_UNSUPPORTED (options unchanged) if no candidate converges on the sample.
+ */
+typedef struct {
+  int precond;              /* FEHMM_PRECOND_* */
+  double mg_omega;
+  double cg_rtol;
+  int mg_reuse;
+  double seconds_per_solve; /* measured: batch time / sample points, of the chosen setting */
+  int from_cache;           /* 1: taken from the cache file, nothing timed */
+  int candidates;           /* settings timed */
+} fehmm_tune_result;
+int fehmm_autotune(fehmm_ctx* ctx, const double* F, int n_sample, const char* cache_path, fehmm_tune_result* best,
+                   void* stream);
+
 /* Number of kernel launches this context has issued since creation (for accounting). */
 long long fehmm_launch_count(const fehmm_ctx* ctx);
 

@@ -41,6 +41,15 @@ class Options(ctypes.Structure):
                 ("mg_reuse", ctypes.c_int)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("precond", ctypes.c_int), ("mg_omega", ctypes.c_double), ("cg_rtol", ctypes.c_double),
+                ("mg_reuse", ctypes.c_int), ("seconds_per_solve", ctypes.c_double), ("from_cache", ctypes.c_int),
+                ("candidates", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _SIGS = {
@@ -66,6 +75,7 @@ _SIGS = {
     "fehmm_macro_solve": (_I, [_P, _P, _P, _P, _P, ctypes.c_double, _I, _P]),
     "fehmm_macro_csr": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "fehmm_launch_count": (ctypes.c_longlong, [_P]),
+    "fehmm_autotune": (_I, [_P, _P, _I, ctypes.c_char_p, ctypes.POINTER(TuneResult), _P]),
     "fehmm_status_str": (ctypes.c_char_p, [_I]),
     "fehmm_rve_solve_list": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P]),
     "fehmm_select": (_I, [_P, _I, _I, _I, _P, _P, _P]),
@@ -254,6 +264,16 @@ class Context:
         _check(lib().fehmm_fluctuation(self._h, int(q), int(committed), ctypes.byref(ptr), ctypes.byref(n)),
                "fluctuation")
         return torch.as_tensor(_DevArray(ptr.value, n.value, "<f8"), device="cuda")
+
+    def autotune(self, F, n_sample=0, cache_path=None, stream=None) -> dict:
+        """Time candidate solver settings on a sample of the bound points at Fbar = F and keep the
+        fastest that converges (fehmm_autotune); returns the choice."""
+        import torch
+        r = TuneResult()
+        _check(lib().fehmm_autotune(self._h, _dev(F, torch.float64, "F"), int(n_sample),
+                                    cache_path.encode() if cache_path else None, ctypes.byref(r), _stream(stream)),
+               "autotune")
+        return r.as_dict()
 
     def fluctuations(self, committed: bool = False):
         """Device view (torch float64, no copy) of every point's fluctuation, concatenated."""

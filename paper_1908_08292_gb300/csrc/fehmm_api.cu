@@ -1,11 +1,13 @@
 // C ABI of the batched FE-HMM RVE engine (declarations and contracts in include/fehmm.h).
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <numeric>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "fehmm.h"
@@ -589,6 +591,206 @@ int fehmm_macro_csr(fehmm_ctx* c, const int32_t** rowptr, const int32_t** col, i
 }
 
 long long fehmm_launch_count(const fehmm_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------ autotuner
+namespace {
+
+// Cache key: everything the choice depends on besides the deformation (problem class, grids,
+// device).  One text line per tuned configuration: "<key>\t<precond> <mg_omega> <cg_rtol>
+// <mg_reuse> <seconds per RVE solve>"; the last matching line wins.
+std::string tune_key(const fehmm_ctx* c) {
+  std::vector<int> grids(c->rve_n.begin(), c->rve_n.end());
+  std::sort(grids.begin(), grids.end());
+  grids.erase(std::unique(grids.begin(), grids.end()), grids.end());
+  cudaDeviceProp prop;
+  const char* dev = cudaGetDeviceProperties(&prop, c->device) == cudaSuccess ? prop.name : "unknown";
+  char buf[256];
+  snprintf(buf, sizeof(buf), "dim=%d prec=%d law=%d bc=%d grids=", c->opt.dim, c->opt.precision, c->opt.law, c->opt.bc);
+  std::string key(buf);
+  for (size_t k = 0; k < grids.size(); ++k) key += (k ? "," : "") + std::to_string(grids[k]);
+  key += " dev=";
+  key += dev;
+  for (char& ch : key)
+    if (ch == '\t' || ch == '\n') ch = ' ';
+  return key;
+}
+
+bool tune_cache_lookup(const char* path, const std::string& key, fehmm_tune_result* r) {
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  bool found = false;
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    char* tab = strchr(line, '\t');
+    if (!tab) continue;
+    *tab = 0;
+    if (key != line) continue;
+    fehmm_tune_result t{};
+    if (sscanf(tab + 1, "%d %lf %lf %d %lf", &t.precond, &t.mg_omega, &t.cg_rtol, &t.mg_reuse, &t.seconds_per_solve) ==
+        5) {
+      *r = t;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_cache_store(const char* path, const std::string& key, const fehmm_tune_result& r) {
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s\t%d %.17g %.17g %d %.9g\n", key.c_str(), r.precond, r.mg_omega, r.cg_rtol, r.mg_reuse,
+          r.seconds_per_solve);
+  fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fehmm_autotune(fehmm_ctx* c, const double* F, int n_sample, const char* cache_path, fehmm_tune_result* out,
+                   void* stream) {
+  if (!c || !F) return FEHMM_ERR_ARG;
+  if (c->n_qp <= 0) return FEHMM_ERR_STATE;
+  const std::string key = tune_key(c);
+  fehmm_tune_result best{};
+  if (tune_cache_lookup(cache_path, key, &best)) {
+    fehmm_options o = c->opt;
+    o.precond = best.precond;
+    o.mg_omega = best.mg_omega;
+    o.cg_rtol = best.cg_rtol;
+    o.mg_reuse = best.mg_reuse;
+    if (!valid_options(&o)) return FEHMM_ERR_ARG;
+    c->opt = o;
+    best.from_cache = 1;
+    best.candidates = 0;
+    if (out) *out = best;
+    return FEHMM_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = c->opt.dim, n_qp = c->n_qp;
+  const int ns = n_sample > 0 ? std::min(n_sample, n_qp) : std::min(n_qp, 2 * c->num_sms);
+  // an evenly strided sample of the bound points (covers every grid size of a mixed batch)
+  std::vector<int32_t> list(ns);
+  for (int k = 0; k < ns; ++k) list[k] = (int32_t)(((long long)k * n_qp) / ns);
+  int32_t* d_list = nullptr;
+  int32_t* d_status = nullptr;
+  double *d_P = nullptr, *d_A = nullptr, *d_save = nullptr;
+  int32_t cnt = ns;
+  int rc = FEHMM_OK;
+  const size_t nA = (size_t)n_qp * d * d * d * d;
+  if (cudaMalloc((void**)&d_list, sizeof(int32_t) * (ns + 1)) != cudaSuccess ||
+      cudaMalloc((void**)&d_status, sizeof(int32_t) * n_qp) != cudaSuccess ||
+      cudaMalloc((void**)&d_P, sizeof(double) * (size_t)n_qp * d * d) != cudaSuccess ||
+      cudaMalloc((void**)&d_A, sizeof(double) * nA) != cudaSuccess ||
+      cudaMalloc((void**)&d_save, sizeof(double) * c->w_total) != cudaSuccess) {
+    cudaGetLastError();
+    rc = FEHMM_ERR_OOM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == FEHMM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = FEHMM_ERR_CUDA;
+  if (rc == FEHMM_OK &&
+      (cudaMemcpyAsync(d_list, list.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaMemcpyAsync(d_list + ns, &cnt, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaMemcpyAsync(d_save, c->d_w_cur, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    rc = FEHMM_ERR_CUDA;
+  // candidates: the preconditioner, the smoother damping (below the positive-definiteness bound of
+  // each element type), the coarse-level reuse (3D), the Newton-correction PCG tolerance
+  struct Cand {
+    int precond;
+    double omega, cg_rtol;
+    int reuse;
+  };
+  std::vector<Cand> cands;
+  const fehmm_options base = c->opt;
+  const double cgr[3] = {base.cg_rtol, base.cg_rtol * 10.0, base.cg_rtol * 0.1};
+  const double om2[4] = {0.5, 0.6, 0.7, 0.8}, om3[4] = {0.45, 0.55, 0.6, 0.65};
+  for (int kc = 0; kc < 3; ++kc) {
+    if (!(cgr[kc] > 0 && cgr[kc] < 0.5)) continue;
+    for (int ko = 0; ko < 4; ++ko)
+      for (int reuse = (d == 3 ? 0 : 1); reuse <= 1; ++reuse)
+        cands.push_back({FEHMM_PRECOND_MULTIGRID, d == 2 ? om2[ko] : om3[ko], cgr[kc], reuse});
+    cands.push_back({FEHMM_PRECOND_BLOCK_JACOBI, base.mg_omega, cgr[kc], base.mg_reuse});
+  }
+  double best_t = 1e300;
+  int n_ok = 0;
+  std::vector<int32_t> st(n_qp);
+  for (size_t k = 0; rc == FEHMM_OK && k < cands.size(); ++k) {
+    fehmm_options o = base;
+    o.precond = cands[k].precond;
+    o.mg_omega = cands[k].omega;
+    o.cg_rtol = cands[k].cg_rtol;
+    o.mg_reuse = cands[k].reuse;
+    if (!valid_options(&o)) continue;
+    c->opt = o;
+    float ms = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {  // the first run warms up, the second is timed
+      if (cudaMemsetAsync(d_status, 0xff, sizeof(int32_t) * n_qp, s) != cudaSuccess ||
+          cudaEventRecord(e0, s) != cudaSuccess) {
+        rc = FEHMM_ERR_CUDA;
+        break;
+      }
+      const int r = rve_solve_impl(c, F, d_P, d_A, nullptr, d_status, nullptr, FEHMM_SOLVE_FROM_COMMITTED, d_list,
+                                   d_list + ns, stream);
+      if (r != FEHMM_OK || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = r != FEHMM_OK ? r : FEHMM_ERR_CUDA;
+        break;
+      }
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (cudaMemcpy(st.data(), d_status, sizeof(int32_t) * n_qp, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = FEHMM_ERR_CUDA;
+        break;
+      }
+      for (int q : list) ok = ok && st[q] == FEHMM_RVE_OK;
+    }
+    if (rc != FEHMM_OK) break;
+    if (!ok) continue;  // a setting that does not converge on the sample is never chosen
+    ++n_ok;
+    const double t = ms * 1e-3 / ns;
+    if (t < best_t) {
+      best_t = t;
+      best.precond = o.precond;
+      best.mg_omega = o.mg_omega;
+      best.cg_rtol = o.cg_rtol;
+      best.mg_reuse = o.mg_reuse;
+      best.seconds_per_solve = t;
+    }
+  }
+  // the current fluctuations as before the trials
+  if (rc == FEHMM_OK && cudaMemcpyAsync(c->d_w_cur, d_save, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    rc = FEHMM_ERR_CUDA;
+  if (rc == FEHMM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = FEHMM_ERR_CUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(d_list);
+  dfree(d_status);
+  dfree(d_P);
+  dfree(d_A);
+  dfree(d_save);
+  if (rc == FEHMM_OK && n_ok == 0) rc = FEHMM_ERR_UNSUPPORTED;  // nothing converged: keep the options
+  if (rc != FEHMM_OK) {
+    cudaGetLastError();
+    c->opt = base;
+    return rc;
+  }
+  fehmm_options o = base;
+  o.precond = best.precond;
+  o.mg_omega = best.mg_omega;
+  o.cg_rtol = best.cg_rtol;
+  o.mg_reuse = best.mg_reuse;
+  c->opt = o;
+  best.from_cache = 0;
+  best.candidates = (int)cands.size();
+  tune_cache_store(cache_path, key, best);
+  if (out) *out = best;
+  return FEHMM_OK;
+}
 
 const char* fehmm_status_str(int code) {
   switch (code) {
