@@ -131,6 +131,12 @@ typedef struct {
   int mg_reuse;         /* 3D multigrid: 1 (default) builds the coarse levels at the first Newton
                            iteration of a solve and reuses them in the later ones; 0 rebuilds
                            them at every Newton iteration */
+  int transfer_warm;    /* 1 (default): each point keeps the solutions X_c of its tangent-transfer
+                           solves (d^2 fields, in the solve's arithmetic type) as load-step state
+                           beside its fluctuation, and the next solve of that point starts its
+                           transfer PCG from them (the residual b - K X_0, stopped at the same
+                           cond_rtol relative to the right-hand side as from zero); 0: every
+                           transfer PCG starts from zero */
 } fehmm_options;
 
 /* Fill `opt` with defaults for dim (2|3) and precision. */
@@ -195,7 +201,8 @@ int fehmm_rve_solve_list(fehmm_ctx* ctx, const double* F, double* P, double* A, 
 int fehmm_select(const int32_t* mask, int n, int value, int stride, int32_t* list, int32_t* count,
                  void* stream);
 
-/* Load-step state: commit copies current -> committed fluctuations; rollback the reverse. */
+/* Load-step state: commit copies current -> committed fluctuations (and kept transfer
+ * solutions); rollback the reverse. */
 int fehmm_commit(fehmm_ctx* ctx, void* stream);
 int fehmm_rollback(fehmm_ctx* ctx, void* stream);
 
@@ -211,6 +218,12 @@ int fehmm_fluctuation(fehmm_ctx* ctx, int q, int which, double** dev_ptr, int* n
  * bind): which = 0 current, 1 committed.  Lets a caller save and restore the load-step state
  * of Sec. 5.1 (e.g. to repeat a load step from the same converged state). */
 int fehmm_fluctuation_all(fehmm_ctx* ctx, int which, double** dev_ptr, long long* n_values);
+
+/* The kept tangent-transfer solutions of all bound points (see fehmm_options.transfer_warm) as
+ * one device array of n_bytes bytes (owned by the context; which = 0 current, 1 committed;
+ * committed and rolled back together with the fluctuations).  NULL and 0 when transfer_warm was
+ * off at fehmm_bind_qps. */
+int fehmm_transfer_state_all(fehmm_ctx* ctx, int which, void** dev_ptr, long long* n_bytes);
 
 /*
  * Structured macro mesh on [0,1]^dim with n_el[c] elements along axis c (host array of
@@ -350,7 +363,8 @@ int fehmm_surrogate_targets(const fehmm_surrogate_params* sp, const double* F, c
  * change.  The choice is written into the context's options and, when cache_path (host text
  * file, may be NULL) is given, appended to it under a key of dimension, precision, law,
  * coupling, the grid sizes bound and the device name; a later call with a matching key applies
- * the cached choice without timing.  The current fluctuations are restored after the trials.
+ * the cached choice without timing.  The current fluctuations and kept transfer solutions are
+ * restored after the trials.
  * best (host, may be NULL) receives the choice.  Allocates temporary device memory; returns
  * FEHMM_ERR_UNSUPPORTED (options unchanged) if no candidate converges on the sample.
  */

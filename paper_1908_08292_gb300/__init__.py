@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("cond_rtol", ctypes.c_double), ("max_cond_cg", ctypes.c_int),
                 ("retry_stages", ctypes.c_int), ("precond", ctypes.c_int),
                 ("bc", ctypes.c_int), ("law", ctypes.c_int), ("mg_omega", ctypes.c_double),
-                ("mg_reuse", ctypes.c_int)]
+                ("mg_reuse", ctypes.c_int), ("transfer_warm", ctypes.c_int)]
 
 
 class TuneResult(ctypes.Structure):
@@ -65,6 +65,7 @@ _SIGS = {
     "fehmm_rollback": (_I, [_P, _P]),
     "fehmm_fluctuation": (_I, [_P, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_I)]),
     "fehmm_fluctuation_all": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_longlong)]),
+    "fehmm_transfer_state_all": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_longlong)]),
     "fehmm_macro_create": (_I, [_P, _P]),
     "fehmm_macro_qp_F": (_I, [_P, _P, _P, _P]),
     "fehmm_macro_assemble": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -282,6 +283,16 @@ class Context:
         _check(lib().fehmm_fluctuation_all(self._h, int(committed), ctypes.byref(ptr), ctypes.byref(n)),
                "fluctuation_all")
         return torch.as_tensor(_DevArray(ptr.value, n.value, "<f8"), device="cuda")
+
+    def transfer_state(self, committed: bool = False):
+        """Device view (torch uint8, no copy) of the kept tangent-transfer solutions, or None."""
+        import torch
+        ptr, n = _P(), ctypes.c_longlong()
+        _check(lib().fehmm_transfer_state_all(self._h, int(committed), ctypes.byref(ptr), ctypes.byref(n)),
+               "transfer_state_all")
+        if not ptr.value or n.value == 0:
+            return None
+        return torch.as_tensor(_DevArray(ptr.value, n.value, "|u1"), device="cuda")
 
     # ------------------------------------------------------------------ macro
     def macro_create(self, n_el):

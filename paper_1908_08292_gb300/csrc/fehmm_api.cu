@@ -37,6 +37,9 @@ struct fehmm_ctx {
   int64_t* d_w_off = nullptr;
   double* d_w_cur = nullptr;
   double* d_w_comm = nullptr;
+  void* d_x_cur = nullptr;  // kept tangent-transfer solutions (fehmm_options.transfer_warm)
+  void* d_x_comm = nullptr;
+  size_t x_bytes = 0;
   int32_t* d_queue = nullptr;
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -85,7 +88,7 @@ bool valid_options(const fehmm_options* o) {
          (o->precond == FEHMM_PRECOND_BLOCK_JACOBI || o->precond == FEHMM_PRECOND_MULTIGRID) &&
          (o->bc == FEHMM_BC_PERIODIC || o->bc == FEHMM_BC_KUBC) &&
          (o->law == FEHMM_LAW_NEO_HOOKE || o->law == FEHMM_LAW_SVK) && o->mg_omega > 0.0 && o->mg_omega < 1.0 &&
-         (o->mg_reuse == 0 || o->mg_reuse == 1);
+         (o->mg_reuse == 0 || o->mg_reuse == 1) && (o->transfer_warm == 0 || o->transfer_warm == 1);
 }
 
 }  // namespace
@@ -110,6 +113,7 @@ int fehmm_default_options(fehmm_options* opt, int dim, int precision) {
   opt->law = FEHMM_LAW_NEO_HOOKE;
   opt->mg_omega = dim == 2 ? 0.7 : 0.6;
   opt->mg_reuse = 1;
+  opt->transfer_warm = 1;
   return FEHMM_OK;
 }
 
@@ -145,6 +149,8 @@ int fehmm_destroy(fehmm_ctx* c) {
   dfree(c->d_w_off);
   dfree(c->d_w_cur);
   dfree(c->d_w_comm);
+  if (c->d_x_cur) cudaFree(c->d_x_cur);
+  if (c->d_x_comm) cudaFree(c->d_x_comm);
   dfree(c->d_queue);
   if (c->d_scratch) cudaFree(c->d_scratch);
   dfree(c->d_rowptr);
@@ -259,6 +265,25 @@ int fehmm_bind_qps(fehmm_ctx* c, int n_qp, const int32_t* rve_of_qp) {
   if (cudaMemset(c->d_w_cur, 0, sizeof(double) * total) != cudaSuccess ||
       cudaMemset(c->d_w_comm, 0, sizeof(double) * total) != cudaSuccess)
     return FEHMM_ERR_CUDA;
+  // kept tangent-transfer solutions: d*d fields of the point's dofs, in the solve's arithmetic type
+  if (c->d_x_cur) cudaFree(c->d_x_cur);
+  if (c->d_x_comm) cudaFree(c->d_x_comm);
+  c->d_x_cur = c->d_x_comm = nullptr;
+  c->x_bytes = 0;
+  if (c->opt.transfer_warm) {
+    const size_t xb = total * (size_t)(d * d) * (c->opt.precision == FEHMM_PREC_MIXED ? sizeof(float) : sizeof(double));
+    if (cudaMalloc(&c->d_x_cur, xb) != cudaSuccess || cudaMalloc(&c->d_x_comm, xb) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->d_x_cur) cudaFree(c->d_x_cur);
+      if (c->d_x_comm) cudaFree(c->d_x_comm);
+      c->d_x_cur = c->d_x_comm = nullptr;
+      c->n_qp = 0;
+      return FEHMM_ERR_OOM;
+    }
+    if (cudaMemset(c->d_x_cur, 0, xb) != cudaSuccess || cudaMemset(c->d_x_comm, 0, xb) != cudaSuccess)
+      return FEHMM_ERR_CUDA;
+    c->x_bytes = xb;
+  }
   const int blocks = std::min(n_qp, c->num_sms);
   const bool mixed = c->opt.precision == FEHMM_PREC_MIXED;
   const size_t sb = d == 2 ? rve2d_scratch_bytes(nn_max, mixed, blocks) : rve3d_scratch_bytes(nn_max, mixed, blocks);
@@ -314,6 +339,9 @@ static int rve_solve_impl(fehmm_ctx* c, const double* F, double* P, double* A, d
   a.qp_w_off = c->d_w_off;
   a.w_in = (flags & FEHMM_SOLVE_FROM_COMMITTED) ? c->d_w_comm : c->d_w_cur;
   a.w_out = c->d_w_cur;
+  const bool warm = c->opt.transfer_warm && c->d_x_cur;
+  a.X_in = warm ? ((flags & FEHMM_SOLVE_FROM_COMMITTED) ? c->d_x_comm : c->d_x_cur) : nullptr;
+  a.X_out = c->d_x_cur;
   a.F = F;
   a.P = P;
   a.A = (flags & FEHMM_SOLVE_NO_TANGENT) ? nullptr : A;
@@ -352,19 +380,34 @@ static int rve_solve_impl(fehmm_ctx* c, const double* F, double* P, double* A, d
 int fehmm_commit(fehmm_ctx* c, void* stream) {
   if (!c) return FEHMM_ERR_ARG;
   if (c->n_qp <= 0) return FEHMM_ERR_STATE;
-  return cudaMemcpyAsync(c->d_w_comm, c->d_w_cur, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice,
-                         (cudaStream_t)stream) == cudaSuccess
-             ? FEHMM_OK
-             : FEHMM_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(c->d_w_comm, c->d_w_cur, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess ||
+      (c->x_bytes && cudaMemcpyAsync(c->d_x_comm, c->d_x_cur, c->x_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)) {
+    cudaGetLastError();
+    return FEHMM_ERR_CUDA;
+  }
+  return FEHMM_OK;
 }
 
 int fehmm_rollback(fehmm_ctx* c, void* stream) {
   if (!c) return FEHMM_ERR_ARG;
   if (c->n_qp <= 0) return FEHMM_ERR_STATE;
-  return cudaMemcpyAsync(c->d_w_cur, c->d_w_comm, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice,
-                         (cudaStream_t)stream) == cudaSuccess
-             ? FEHMM_OK
-             : FEHMM_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(c->d_w_cur, c->d_w_comm, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess ||
+      (c->x_bytes && cudaMemcpyAsync(c->d_x_cur, c->d_x_comm, c->x_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)) {
+    cudaGetLastError();
+    return FEHMM_ERR_CUDA;
+  }
+  return FEHMM_OK;
+}
+
+int fehmm_transfer_state_all(fehmm_ctx* c, int which, void** dev_ptr, long long* n_bytes) {
+  if (!c || !dev_ptr || (which != 0 && which != 1) || c->n_qp <= 0) return FEHMM_ERR_ARG;
+  *dev_ptr = which ? c->d_x_comm : c->d_x_cur;
+  if (n_bytes) *n_bytes = (long long)c->x_bytes;
+  return FEHMM_OK;
 }
 
 int fehmm_fluctuation(fehmm_ctx* c, int q, int which, double** dev_ptr, int* n_values) {
@@ -680,6 +723,7 @@ int fehmm_autotune(fehmm_ctx* c, const double* F, int n_sample, const char* cach
   int32_t* d_list = nullptr;
   int32_t* d_status = nullptr;
   double *d_P = nullptr, *d_A = nullptr, *d_save = nullptr;
+  void* d_xsave = nullptr;
   int32_t cnt = ns;
   int rc = FEHMM_OK;
   const size_t nA = (size_t)n_qp * d * d * d * d;
@@ -687,7 +731,8 @@ int fehmm_autotune(fehmm_ctx* c, const double* F, int n_sample, const char* cach
       cudaMalloc((void**)&d_status, sizeof(int32_t) * n_qp) != cudaSuccess ||
       cudaMalloc((void**)&d_P, sizeof(double) * (size_t)n_qp * d * d) != cudaSuccess ||
       cudaMalloc((void**)&d_A, sizeof(double) * nA) != cudaSuccess ||
-      cudaMalloc((void**)&d_save, sizeof(double) * c->w_total) != cudaSuccess) {
+      cudaMalloc((void**)&d_save, sizeof(double) * c->w_total) != cudaSuccess ||
+      (c->x_bytes && cudaMalloc(&d_xsave, c->x_bytes) != cudaSuccess)) {
     cudaGetLastError();
     rc = FEHMM_ERR_OOM;
   }
@@ -697,6 +742,7 @@ int fehmm_autotune(fehmm_ctx* c, const double* F, int n_sample, const char* cach
       (cudaMemcpyAsync(d_list, list.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s) != cudaSuccess ||
        cudaMemcpyAsync(d_list + ns, &cnt, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
        cudaMemcpyAsync(d_save, c->d_w_cur, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+       (c->x_bytes && cudaMemcpyAsync(d_xsave, c->d_x_cur, c->x_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ||
        cudaStreamSynchronize(s) != cudaSuccess))
     rc = FEHMM_ERR_CUDA;
   // candidates: the preconditioner, the smoother damping (below the positive-definiteness bound of
@@ -762,8 +808,10 @@ int fehmm_autotune(fehmm_ctx* c, const double* F, int n_sample, const char* cach
       best.seconds_per_solve = t;
     }
   }
-  // the current fluctuations as before the trials
-  if (rc == FEHMM_OK && cudaMemcpyAsync(c->d_w_cur, d_save, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+  // the current fluctuations (and kept transfer solutions) as before the trials
+  if (rc == FEHMM_OK &&
+      (cudaMemcpyAsync(c->d_w_cur, d_save, sizeof(double) * c->w_total, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+       (c->x_bytes && cudaMemcpyAsync(c->d_x_cur, d_xsave, c->x_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)))
     rc = FEHMM_ERR_CUDA;
   if (rc == FEHMM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = FEHMM_ERR_CUDA;
   if (e0) cudaEventDestroy(e0);
@@ -773,6 +821,7 @@ int fehmm_autotune(fehmm_ctx* c, const double* F, int n_sample, const char* cach
   dfree(d_P);
   dfree(d_A);
   dfree(d_save);
+  if (d_xsave) cudaFree(d_xsave);
   if (rc == FEHMM_OK && n_ok == 0) rc = FEHMM_ERR_UNSUPPORTED;  // nothing converged: keep the options
   if (rc != FEHMM_OK) {
     cudaGetLastError();

@@ -121,6 +121,8 @@ extern "C" int fehmm_rve2d_solve_fp64_noalloc(int n_qp, int grid_n, int phase_pe
   a.law = 0;
   a.mg_omega = 0.7f;
   a.mg_reuse = 0;
+  a.X_in = nullptr;  // no kept transfer solutions: every transfer solve starts from zero
+  a.X_out = nullptr;
   a.scratch_stride = 72LL * a.nn_max;
   a.flags = A ? 0 : kFlagNoTangent;
   // the shared work counter keeps the previous call's value: clear it on this stream

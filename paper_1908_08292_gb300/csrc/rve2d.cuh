@@ -916,11 +916,14 @@ __device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
 // negative curvature (p^T K p <= 0) the iteration stops with the step built so far
 // (Steihaug's truncated CG; on the first iteration the preconditioned residual direction with
 // |p^T K p| as curvature) and reports kStatusNegCurv, which the Newton loop accepts.
+// warm: xs holds a start value x0 at the owned nodes (the previous solve's solution); the
+// iteration runs on r = b - K x0 and stops at the same rtol relative to b^T M^-1 b as a start
+// from zero (one more preconditioner application and apply, counted as one iteration).
 template <typename TA, bool REG, bool kMG>
 __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& o, const TA (&Minv)[2][4],
                                         const MgCtx<TA>& mg, const TA (&b)[4],
                         vec2_t<TA>* xs, TA rtol, int max_it, vec2_t<TA>* ps, double* red, int* status,
-                        bool truncate) {
+                        bool truncate, bool warm = false) {
   // x: registers on the block-Jacobi path; accumulated in xs on the multigrid path, where the
   // V-cycle needs the registers
   TA r[4], u[4], w[4], p[4], s[4], x[4];
@@ -943,7 +946,7 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
     }
   };
   if constexpr (kMG) {
-    if (o.active) {
+    if (o.active && !warm) {
       xs[o.node[0]] = mk2<TA>(TA(0), TA(0));
       xs[o.node[1]] = mk2<TA>(TA(0), TA(0));
     }
@@ -1006,6 +1009,31 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
     __syncthreads();   // every read of ps done before the caller's exchange
   };
   *status = kStatusOk;
+  double gref = -1.0;  // stopping reference b^T M^-1 b of a warm start
+  int it = 0;
+  if (warm) {
+    precond();  // u = M^-1 b
+    double unused;
+    block_dot2_fp64<TA>(r[0] * u[0] + r[1] * u[1] + r[2] * u[2] + r[3] * u[3], TA(0), red, gref, unused);
+    if (o.active) {  // u = x0, w = K x0, r = b - K x0
+      const vec2_t<TA> x0 = xs[o.node[0]], x1 = xs[o.node[1]];
+      u[0] = x0.x;
+      u[1] = x0.y;
+      u[2] = x1.x;
+      u[3] = x1.y;
+    } else {
+      u[0] = u[1] = u[2] = u[3] = TA(0);
+    }
+    if constexpr (!kMG) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[k] = u[k];
+    }
+    exchange_apply();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[k] -= w[k];
+    __syncthreads();  // every read of ps done before the next exchange
+    it = 1;
+  }
   precond();
   exchange_apply();
   // inner products: per thread and per warp in TA, over the block in FP64 (block_dot2_fp64); the
@@ -1015,11 +1043,11 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
                       w[0] * u[0] + w[1] * u[1] + w[2] * u[2] + w[3] * u[3], red, gd, dd);
   TA gamma = (TA)gd, delta = (TA)dd;
   const double gamma0 = gd;
-  int it = 0;
+  const double stop = (double)rtol * (double)rtol * (warm ? gref : gamma0);
   // a non-finite preconditioned residual (e.g. a multigrid coarse inverse of an indefinite
   // tangent) is a breakdown, not a converged zero correction
   if (!isfinite(gamma0)) *status = kStatusPcgBreakdown;
-  if (gamma0 > 0.0 && isfinite(gamma0)) {
+  if (gamma0 > 0.0 && isfinite(gamma0) && !(warm && gamma0 <= stop)) {
     if (!(dd > 0.0)) {
       if (truncate && delta < TA(0)) {
         const TA a0 = cg_div<TA>(gamma, -delta);
@@ -1029,7 +1057,6 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
         *status = kStatusPcgBreakdown;
       }
     } else {
-      const double stop = (double)rtol * (double)rtol * gamma0;
       TA alpha = cg_div<TA>(gamma, delta);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -1484,6 +1511,9 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
     const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
     build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb, mg);
     vec2_t<TA>* X = Xs;
+    // kept solutions of this point's previous transfer solves ([4][NN] vec2, zero at first)
+    const bool warm = a.X_in != nullptr;
+    const vec2_t<TA>* X0 = warm ? reinterpret_cast<const vec2_t<TA>*>(a.X_in) + 2 * w_off : nullptr;
     for (int c = 0; c < 4; ++c) {
       TA b[4] = {TA(0), TA(0), TA(0), TA(0)};
       if (o.active) {
@@ -1492,10 +1522,15 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
         b[1] = b0.y;
         b[2] = b1.x;
         b[3] = b1.y;
+        if (warm) {
+#pragma unroll
+          for (int s = 0; s < 2; ++s)
+            X[c * NN + o.node[s]] = o.pin[s] ? mk2<TA>(TA(0), TA(0)) : X0[c * NN + o.node[s]];
+        }
       }
       int pst = kStatusOk;
       const int ci = pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, X + c * NN, (TA)a.cond_rtol, a.max_cond_cg, sm.p,
-                                            redD, &pst, false);
+                                            redD, &pst, false, warm);
       cond_total += ci;
       cond_max = ci > cond_max ? ci : cond_max;
       if (pst != kStatusOk && status == kStatusOk) status = pst;
@@ -1525,6 +1560,10 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
     const double2 wv = sm.w[v];
     w_out[2 * v] = wv.x;
     w_out[2 * v + 1] = wv.y;
+  }
+  if (want_A && a.X_out) {  // the transfer solutions, kept as the next solve's start values
+    vec2_t<TA>* Xo = reinterpret_cast<vec2_t<TA>*>(a.X_out) + 2 * w_off;
+    for (int v = tid; v < 4 * NN; v += blockDim.x) Xo[v] = Xs[v];
   }
   if (tid == 0) {
     a.status[qp] = status;

@@ -1182,7 +1182,7 @@ __device__ __noinline__ void mg3_vcycle_fine(const Ctx3<TA>& c, const TA* r) {
 
 // Chronopoulos-Gear PCG for K x = b; b given in sc.r on entry (overwritten), x in sc.x.
 template <typename TA, int LAW>
-__device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* status) {
+__device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* status, bool warm = false) {
   const int NN = c.g.NN;
   TA* x = c.sc.x;
   TA* r = c.sc.r;
@@ -1212,15 +1212,39 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
     }
     block_dot2_fp64<TA>(g, d, c.red + 2 * 512 - 64, gam, del);
   };
-  for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) x[v] = TA(0);
   *status = kStatusOk;
+  double gref = -1.0;  // stopping reference b^T M^-1 b of a warm start
+  int it = 0;
+  if (!warm) {
+    for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) x[v] = TA(0);
+  } else {
+    // x holds the start value x0 (the previous solve's solution): iterate on r = b - K x0 with
+    // the stopping reference of b (one more preconditioner application and apply, counted)
+    precond_to_vin();
+    {
+      TA g = TA(0);
+      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) g += r[v] * c.vin[v];
+      double unused;
+      block_dot2_fp64<TA>(g, TA(0), c.red + 2 * 512 - 64, gref, unused);
+    }
+    for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.vin[v] = x[v];
+    __syncthreads();
+    apply3<TA, LAW>(c, 0, 0);
+    for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) r[v] -= c.vout[v];
+    __syncthreads();
+    it = 1;
+  }
   precond_to_vin();
   apply3<TA, LAW>(c, 0, 0);
   double gd, dd;
   dots(gd, dd);
   TA gamma = (TA)gd, delta = (TA)dd;
   const double gamma0 = gd;
-  int it = 0;
+  const double stop = (double)rtol * (double)rtol * (warm ? gref : gamma0);
+  if (warm && gamma0 <= stop) {  // the start value already meets the tolerance
+    __syncthreads();
+    return it;
+  }
   if (!isfinite(gamma0)) {  // non-finite preconditioned residual: a breakdown
     *status = kStatusPcgBreakdown;
     __syncthreads();
@@ -1238,7 +1262,6 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
     __syncthreads();
     return 0;
   }
-  const double stop = (double)rtol * (double)rtol * gamma0;
   TA alpha = div3(gamma, delta), beta = TA(0);
   for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
     p[v] = c.vin[v];
@@ -1452,11 +1475,21 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
     __syncthreads();
     // LX[c][c'] = L_c . X_c', X_c' = -K^-1 L_c'  (kept in shared memory: misc[16 + 9c + c'])
     double* LX = misc + 16;
+    // kept solutions of this point's previous transfer solves ([9][3][NN], zero at first) start
+    // the PCG and receive the new ones
+    const bool warm = a.X_in != nullptr;
+    const TA* X0 = warm ? reinterpret_cast<const TA*>(a.X_in) + 9 * (size_t)a.qp_w_off[qp] : nullptr;
+    TA* X1 = a.X_out ? reinterpret_cast<TA*>(a.X_out) + 9 * (size_t)a.qp_w_off[qp] : nullptr;
     for (int cp = 0; cp < 9; ++cp) {
-      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.r[v] = -c.sc.L[(size_t)cp * 3 * NN + v];
+      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
+        c.sc.r[v] = -c.sc.L[(size_t)cp * 3 * NN + v];
+        if (warm) c.sc.x[v] = X0[(size_t)cp * 3 * NN + v];
+      }
       __syncthreads();
       int pst = kStatusOk;
-      const int ci = pcg3<TA, LAW>(c, (TA)a.cond_rtol, a.max_cond_cg, false, &pst);
+      const int ci = pcg3<TA, LAW>(c, (TA)a.cond_rtol, a.max_cond_cg, false, &pst, warm);
+      if (X1)
+        for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) X1[(size_t)cp * 3 * NN + v] = c.sc.x[v];
       cond_total += ci;
       cond_max = ci > cond_max ? ci : cond_max;
       if (pst != kStatusOk && status == kStatusOk) status = pst;

@@ -38,6 +38,9 @@ struct Rve2dArgs {
   int law;            // 0 neo-Hookean, 1 St. Venant-Kirchhoff
   float mg_omega;     // smoother damping of the multigrid V-cycle
   int mg_reuse;       // 3D: reuse the coarse levels over the Newton iterations of a solve
+  const void* X_in;   // kept tangent-transfer solutions (TA) to start from, or null (start from 0);
+                      // per point at (2D: 4, 3D: 9) x qp_w_off[qp], layout [d*d][NN][d]
+  void* X_out;        // where the new transfer solutions go (may alias X_in; null: not kept)
 };
 
 size_t rve2d_smem_bytes(int nn_max, bool mixed);

@@ -162,14 +162,18 @@ class LoadStepDriver:
         return passes
 
     def state(self):
-        """Copy of the load-step state (macro u, committed fluctuations, last tangent) to repeat a step."""
-        return (self.u.clone(), self.ctx.fluctuations(committed=True).clone(), self.K.clone(), self.K_valid,
-                self.scale)
+        """Copy of the load-step state (macro u, committed fluctuations and kept transfer solutions, last
+        tangent) to repeat a step."""
+        xs = self.ctx.transfer_state(committed=True)
+        return (self.u.clone(), self.ctx.fluctuations(committed=True).clone(), None if xs is None else xs.clone(),
+                self.K.clone(), self.K_valid, self.scale)
 
     def restore(self, st):
-        u, w, K, kv, scale = st
+        u, w, xs, K, kv, scale = st
         self.u.copy_(u)
         self.ctx.fluctuations(committed=True).copy_(w)
+        if xs is not None:
+            self.ctx.transfer_state(committed=True).copy_(xs)
         self.ctx.rollback()
         self.K.copy_(K)
         self.K_valid, self.scale = kv, scale
