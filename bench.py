@@ -942,6 +942,80 @@ def run_c5(args):
     }))
 
 
+def run_hconv(args):
+    """Micro mesh convergence (the a-priori estimates of Sec. 4, the micro-convergence studies of
+    Sec. 6): one microstructure, a box inclusion [0.25, 0.75)^d of stiffness ratio 10 that every
+    grid n = 4, 8, ... resolves exactly, solved on the GPU in FP64 at a finite-strain Fbar with
+    periodic and with KUBC coupling; relative errors of Pbar and Abar against the finest grid and
+    the observed orders.  Also the modelling error of KUBC (Eq. ModelingError): the KUBC-periodic
+    gap of Abar on k x k tilings of one cell, and the macro displacement of the config-1 problem
+    computed with RVE grids 8, 16, 32 of the same microstructure."""
+    import dataclasses
+
+    import torch
+
+    import paper_1908_08292_gb300 as fe
+    import synth
+    from paper_1908_08292_gb300.driver import LoadStepDriver
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    strict = dict(newton_rtol=1e-13, newton_atol=1e-15, cg_rtol=1e-9, cond_rtol=1e-12)
+    Fs = {2: np.array([[1.12, 0.06], [0.03, 0.95]]),
+          3: np.array([[1.10, 0.05, 0.0], [0.02, 0.96, 0.03], [0.0, 0.01, 0.97]])}
+    grids = {2: [4, 8, 16, 32], 3: [4, 8, 16]}
+
+    def batch(dim, ns, phases, bc):
+        n_q = len(ns)
+        with fe.Context(dim, "fp64", bc=bc, **strict) as ctx:
+            ctx.add_rves(ns, phases, [[1.0, 10.0]] * n_q, [[0.3, 0.3]] * n_q)
+            ctx.bind_qps(np.arange(n_q, dtype=np.int32))
+            F = torch.tensor(np.stack([Fs[dim]] * n_q).reshape(n_q, -1), dtype=torch.float64, device=dev)
+            P = torch.zeros(n_q, dim * dim, dtype=torch.float64, device=dev)
+            A = torch.zeros(n_q, dim ** 4, dtype=torch.float64, device=dev)
+            st = torch.zeros(n_q, dtype=torch.int32, device=dev)
+            ctx.rve_solve(F, P, A, st)
+            torch.cuda.synchronize()
+            assert (st.cpu().numpy() == 0).all()
+            return P.cpu().numpy(), A.cpu().numpy()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    out = {"metric": "micro h-convergence of Pbar and Abar; KUBC modelling error; macro u vs RVE grid",
+           "workload": "hconv", "n_gpus": 1, "unit": "relative error", "higher_is_better": False, "studies": []}
+    for dim in (2, 3):
+        ns = grids[dim]
+        for bc, name in ((0, "periodic"), (1, "KUBC")):
+            P, A = batch(dim, ns, [synth.box_inclusion(n, dim) for n in ns], bc)
+            eP = [rel(P[k], P[-1]) for k in range(len(ns) - 1)]
+            eA = [rel(A[k], A[-1]) for k in range(len(ns) - 1)]
+            out["studies"].append({"dim": dim, "coupling": name, "grids": ns, "reference": ns[-1],
+                                   "err_P": eP, "err_A": eA,
+                                   "order_A": [float(np.log2(eA[k] / eA[k + 1])) for k in range(len(eA) - 1)]})
+    # KUBC modelling error: k x k tilings of the 8 x 8 cell (the periodic result is tiling-invariant)
+    ks = [1, 2, 4]
+    tiles = [np.tile(synth.box_inclusion(8, 2).reshape(8, 8), (k, k)).reshape(-1) for k in ks]
+    _, Ap = batch(2, [8 * k for k in ks], tiles, 0)
+    _, Ak = batch(2, [8 * k for k in ks], tiles, 1)
+    out["kubc_gap"] = {"tilings": ks, "gap_A": [rel(Ak[j], Ap[j]) for j in range(len(ks))],
+                       "periodic_tiling_invariance": [rel(Ap[j], Ap[0]) for j in range(len(ks))]}
+    # the macro problem of config 1 with RVE grids 8, 16, 32 of the box microstructure
+    base = synth.config1()
+    us = {}
+    for n in (8, 16, 32):
+        p = dataclasses.replace(base, rve_n=np.array([n]), rve_phase=[synth.box_inclusion(n, 2)])
+        drv = LoadStepDriver(p, precision="fp64", newton_rtol=1e-12, newton_atol=1e-15, cg_rtol=1e-9, cond_rtol=1e-11)
+        try:
+            for k in range(1, p.n_steps + 1):
+                assert drv.load_step(k)["converged"]
+            us[n] = drv.u.cpu().numpy()
+        finally:
+            drv.close()
+    out["macro_u"] = {"rve_grids": [8, 16], "reference": 32,
+                      "err_u": [rel(us[n], us[32]) for n in (8, 16)]}
+    print(json.dumps(out))
+
+
 def run_schemes(args):
     """Algorithm 1 (nested) vs Algorithm 2 (alternating) on full load paths: macro iterations,
     micro Newton iterations and wall time per scheme (the structure of the paper's speed-up
@@ -1007,10 +1081,11 @@ def main():
                          "of --step-index from the zero state (short runs for profiling)")
     ap.add_argument("--precond", default="mg", choices=["mg", "jacobi"],
                     help="RVE PCG preconditioner: multigrid V-cycle (default; 2D) or block-Jacobi")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "schemes"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "schemes", "hconv"],
                     help="c2: 2D 4096 RVEs of 32x32 (default, the headline); c3: 3D 4096 uneven Hex8 RVEs; "
                          "c4: surrogate training; c5: surrogate+fallback vs plain macro iteration; "
-                         "schemes: nested vs alternating load paths")
+                         "schemes: nested vs alternating load paths; hconv: micro mesh convergence and the KUBC "
+                         "modelling error")
     ap.add_argument("--c4-samples", type=int, default=40960)
     ap.add_argument("--c4-holdout", type=int, default=10240)
     ap.add_argument("--c4-epochs", type=int, default=600)
@@ -1028,6 +1103,8 @@ def main():
         run_c4(args)
     elif args.workload == "schemes":
         run_schemes(args)
+    elif args.workload == "hconv":
+        run_hconv(args)
     elif args.workload == "c5":
         _SIZE["macro"] = args.macro if args.macro is not None else 8
         args.macro = _SIZE["macro"]

@@ -228,6 +228,17 @@ def config5(macro: int = 16) -> Problem:
                    20, "mixed", 1e-10, extra={"phi": phi, "F_end": F_end})
 
 
+def box_inclusion(n: int, dim: int, lo: float = 0.25, hi: float = 0.75) -> np.ndarray:
+    """uint8 phase map of an axis-aligned box inclusion [lo, hi)^dim on an n^dim grid (element
+    centroid rule).  With lo, hi multiples of 1/n the pixelised geometry is exact, so a sequence
+    of grids n = 4, 8, 16, ... refines one and the same microstructure (mesh-convergence studies)."""
+    c1 = (np.arange(n) + 0.5) / n
+    inside1 = (c1 >= lo) & (c1 < hi)
+    grids = np.meshgrid(*([inside1] * dim), indexing="ij")
+    inside = np.logical_and.reduce([g.transpose().reshape(-1) for g in grids])
+    return inside.astype(np.uint8)
+
+
 def stretch_ball(seed: int, count: int, radius: float = 0.3, first: int = 0) -> np.ndarray:
     """`count` symmetric right stretch tensors U (count, 3, 3) uniform in the 6-D ball
     ||U - I||_F <= radius (off-diagonal components carry the sqrt(2) weight)."""
