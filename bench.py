@@ -268,7 +268,7 @@ def oracle_parity_and_baseline(p, F, P, A, qps, budget_s, label):
     t0 = time.perf_counter()
     eP, eA, done = [], [], 0
     for q in qps:
-        if time.perf_counter() - t0 > budget_s and done >= 4:
+        if time.perf_counter() - t0 > budget_s and done >= (4 if p.dim == 2 else 1):
             break
         r = p.qp_rve[q]
         Pr, Ar = _oracle_rve((int(p.rve_n[r]), d, p.rve_phase[r], p.rve_E[r], p.rve_nu[r], F[q].reshape(d, d),

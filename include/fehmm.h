@@ -197,19 +197,24 @@ int fehmm_rve_solve_list(fehmm_ctx* ctx, const double* F, double* P, double* A, 
                          const int32_t* count, void* stream);
 
 /* list <- indices q (ascending) with mask[q] == value and q % stride == 0, *count <- their
- * number (device arrays, list of n entries; stride >= 1, e.g. > 1 for an audit sample). */
+ * number (device arrays, list of n entries; stride >= 1, e.g. > 1 for an audit sample).  The
+ * paper has no counterpart: it picks the points of the surrogate path (the learned part of the
+ * workload) that fall back to full RVE solves, or its audit sample. */
 int fehmm_select(const int32_t* mask, int n, int value, int stride, int32_t* list, int32_t* count,
                  void* stream);
 
-/* Load-step state: commit copies current -> committed fluctuations (and kept transfer
- * solutions); rollback the reverse. */
+/* Load-step state (Sec. 5.1: the converged micro state of a load step is the start value of the
+ * next one, the warm start; Sec. 5.2: the alternating scheme carries the last micro iterate).
+ * commit copies current -> committed fluctuations (and kept transfer solutions); rollback the
+ * reverse (e.g. to repeat a load step after a failed macro iteration). */
 int fehmm_commit(fehmm_ctx* ctx, void* stream);
 int fehmm_rollback(fehmm_ctx* ctx, void* stream);
 
 /*
- * Access to the fluctuation of quadrature point q (device pointer to n_node*dim doubles,
- * node-major, owned by the context, valid until the next bind).  which = 0 current,
- * 1 committed.  n_values (optional) receives the length.
+ * Access to the fluctuation of quadrature point q: the periodic micro field w of the kinematics
+ * u = (Fbar - I) X + w (Eq. linearization-uH with the constraints of Eq. ConstraintCondition-
+ * phi_h-phi_H; device pointer to n_node*dim doubles, node-major, owned by the context, valid
+ * until the next bind).  which = 0 current, 1 committed.  n_values (optional) receives the length.
  */
 int fehmm_fluctuation(fehmm_ctx* ctx, int q, int which, double** dev_ptr, int* n_values);
 
@@ -281,7 +286,8 @@ int fehmm_macro_update(fehmm_ctx* ctx, double* u, const double* du, void* stream
 int fehmm_macro_solve(fehmm_ctx* ctx, const double* K_vals, const double* f, double* du, double* info,
                       double rtol, int max_it, void* stream);
 
-/* CSR pattern of the macro tangent (device pointers owned by the context). */
+/* CSR pattern of the assembled macro tangent of Eq. Assem_k_T_IK_mac (one d x d block per pair of
+ * nodes sharing an element; device pointers owned by the context). */
 int fehmm_macro_csr(fehmm_ctx* ctx, const int32_t** rowptr, const int32_t** col, int* n_rows,
                     int* nnz);
 
@@ -338,6 +344,13 @@ typedef struct {
 int fehmm_surrogate_eval(fehmm_mlp* mlp, const fehmm_surrogate_params* sp, const double* F, int n,
                          double* P, double* A, double* W, int32_t* inside, float* work, void* stream);
 size_t fehmm_surrogate_work_floats(int n);
+
+/* Base energy of the surrogate from the RVE's small-strain homogenised tangent A0 (host [81],
+ * iJkL row-major, e.g. from fehmm_rve_solve at F = I): its minor-symmetric part is projected on
+ * isotropy (3K = A_iijj / 3, mu0 = (A_ijij - A_iijj / 3) / 10, lam0 = K - 2 mu0 / 3) and the
+ * remainder A0 - (lam0 1(x)1 + 2 mu0 I^sym) goes to sp->Ca in Mandel form.  Sets sp->lam0, mu0,
+ * Ca only.  FEHMM_ERR_ARG if the projection is not positive definite. */
+int fehmm_surrogate_base_law(const double* A0, fehmm_surrogate_params* sp);
 
 /* Persistence of a trained surrogate (host file path): the packed FP32 network parameters and
  * every field of fehmm_surrogate_params, in a small binary file with a magic and a format

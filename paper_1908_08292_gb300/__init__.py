@@ -91,6 +91,7 @@ _SIGS = {
     "fehmm_mlp_launch_count": (ctypes.c_longlong, [_P]),
     "fehmm_mlp_grad_buffer": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I)]),
     "fehmm_surrogate_save": (_I, [_P, _P, ctypes.c_char_p]),
+    "fehmm_surrogate_base_law": (_I, [_P, _P]),
     "fehmm_surrogate_load": (_I, [_P, _P, ctypes.c_char_p]),
     "fehmm_surrogate_eval": (_I, [_P, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
     "fehmm_surrogate_work_floats": (ctypes.c_size_t, [_I]),

@@ -213,12 +213,15 @@ constexpr int kLawNH = 0, kLawSVK = 1;
 template <int LAW, typename T>
 __device__ __forceinline__ T law2_P(T F00, T F01, T F10, T F11, T lam, T mu, T& P00, T& P01, T& P10, T& P11) {
   if constexpr (LAW == kLawNH) {
-    const NH2<T> q = nh2_eval(F00, F01, F10, F11, lam, mu);
-    P00 = fma(mu, F00, q.hb * q.f00);
-    P01 = fma(mu, F01, q.hb * q.f01);
-    P10 = fma(mu, F10, q.hb * q.f10);
-    P11 = fma(mu, F11, q.hb * q.f11);
-    return q.J;
+    // P = mu F + hb F^-T with F^-T = cof(F) / J, i.e. P = mu F + c cof(F),
+    // c = hb / J = lam J / 2 - (lam / 2 + mu) / J (cof(F) = [[F11, -F10], [-F01, F00]])
+    const T J = F00 * F11 - F01 * F10;
+    const T c = fma(T(0.5) * lam, J, -(T(0.5) * lam + mu) / J);
+    P00 = fma(mu, F00, c * F11);
+    P01 = fma(mu, F01, -c * F10);
+    P10 = fma(mu, F10, -c * F01);
+    P11 = fma(mu, F11, c * F00);
+    return J;
   } else {
     const T c00 = F00 * F00 + F10 * F10, c01 = F00 * F01 + F10 * F11, c11 = F01 * F01 + F11 * F11;
     const T trE = T(0.5) * (c00 + c11) - T(1);
@@ -246,6 +249,7 @@ __device__ __forceinline__ void element_residual(int e, int n, const double2* w,
   const double2 e1 = make_double2((w2.x - w3.x) - d10.x, (w2.y - w3.y) - d10.y);
   const double2 e2 = make_double2((w2.x - w1.x) - d30.x, (w2.y - w1.y) - d30.y);
   double Sa0x = 0, Sa0y = 0, Sa1x = 0, Sa1y = 0, Sb0x = 0, Sb0y = 0, Sb1x = 0, Sb1y = 0;
+  int nbad = 0;
 #pragma unroll
   for (int gy = 0; gy < 2; ++gy) {
     const double t = gauss01(gy);
@@ -258,7 +262,7 @@ __device__ __forceinline__ void element_residual(int e, int n, const double2* w,
       const double F11 = fma(ih, fma(s, e2.y, d30.y), Fb[3]);
       double P00, P01, P10, P11;
       const double J = law2_P<LAW, double>(F00, F01, F10, F11, lam, mu, P00, P01, P10, P11);
-      bad += (J > 0.0) ? 0.0 : 1.0;
+      nbad += (J > 0.0) ? 0 : 1;
       Psum[0] += P00;
       Psum[1] += P01;
       Psum[2] += P10;
@@ -273,6 +277,7 @@ __device__ __forceinline__ void element_residual(int e, int n, const double2* w,
       Sb1y = fma(s, P11, Sb1y);
     }
   }
+  if (nbad) bad += (double)nbad;
   // R_a = (wq / h) P G_a with wq = h^2/4 and G_a the natural-coordinate gradients.
   const double k = 0.25 / ih;
   const int NN = n * n;
@@ -669,20 +674,39 @@ __device__ __forceinline__ void mg_coarse_element(const TA* kf, int nf, int E, T
 __device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 __device__ __forceinline__ int wrap_inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
 
-// y = K_l z at node v = (i, j) of a coarse level (zero at the pinned node).
+// The share of y = K_l z at node (i, j) from the neighbour blocks nb = sub, sub + T, ... (a group
+// of T lanes computes one node; group_sum adds the shares).  Used on the coarse levels, where
+// a level has fewer nodes than the block has threads.
 template <typename TA>
-__device__ __forceinline__ vec2_t<TA> mg_apply(const MgLevel<TA>& L, const vec2_t<TA>* z, int i, int j) {
+__device__ __forceinline__ vec2_t<TA> mg_apply_part(const MgLevel<TA>& L, const vec2_t<TA>* z, int i, int j, int sub,
+                                                    int T) {
   const int n = L.n, v = i + n * j;
   const int cols[3] = {wrap_dec(i, n), i, wrap_inc(i, n)};
   const int rows[3] = {wrap_dec(j, n) * n, j * n, wrap_inc(j, n) * n};
   TA yx = TA(0), yy = TA(0);
-#pragma unroll
-  for (int nb = 0; nb < 9; ++nb) {
+  for (int nb = sub; nb < 9; nb += T) {
     const vec2_t<TA> zn = z[rows[nb / 3] + cols[nb % 3]];
     yx += L.st[(size_t)(nb * 4 + 0) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 1) * L.NN + v] * zn.y;
     yy += L.st[(size_t)(nb * 4 + 2) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 3) * L.NN + v] * zn.y;
   }
-  return pinned2(i, j, L.bc) ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(yx, yy);
+  return mk2<TA>(yx, yy);
+}
+
+// Sum over aligned groups of T lanes (T a power of two dividing 32); all lanes must call it.
+template <typename TA>
+__device__ __forceinline__ vec2_t<TA> group_sum(vec2_t<TA> a, int T) {
+  for (int o = T >> 1; o > 0; o >>= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+  }
+  return a;
+}
+
+// Lanes per node for a coarse level of NN nodes: up to 8, as many as the block's threads allow.
+__device__ __forceinline__ int mg_lanes(int NN) {
+  int T = 1;
+  while (T < 8 && 2 * T * NN <= (int)blockDim.x) T *= 2;
+  return T;
 }
 
 template <typename TA>
@@ -866,9 +890,16 @@ __device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
   const TA om = mg.omega;
   for (int l = 1; l < mg.levels; ++l) {  // descend: residual, restrict (+ next pre-smoothing)
     const MgLevel<TA> v = mg.level(l);
-    if (tid < v.NN) {
-      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, tid % v.n, tid / v.n), rr = v.r[tid];
-      v.t[tid] = mk2<TA>(rr.x - kz.x, rr.y - kz.y);
+    {  // t = r - K z, T lanes per node
+      const int T = mg_lanes(v.NN), node = tid / T, sub = tid % T;
+      const bool on = node < v.NN;
+      const int nd = on ? node : 0, i = nd % v.n, j = nd / v.n;
+      vec2_t<TA> kz = group_sum<TA>(mg_apply_part<TA>(v, v.z, i, j, on ? sub : 9, T), T);
+      if (on && sub == 0) {
+        if (pinned2(i, j, v.bc)) kz = mk2<TA>(TA(0), TA(0));
+        const vec2_t<TA> rr = v.r[nd];
+        v.t[nd] = mk2<TA>(rr.x - kz.x, rr.y - kz.y);
+      }
     }
     __syncthreads();
     if (tid < mg.level(l + 1).NN) mg_restrict_smooth<TA>(mg, l + 1, v.t, v.n, tid);
@@ -897,10 +928,17 @@ __device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
       v.z[tid] = mk2<TA>(zo.x + zp.x, zo.y + zp.y);
     }
     __syncthreads();
-    if (tid < v.NN) {
-      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, i, j), rr = v.r[tid], z = v.z[tid];
-      const vec2_t<TA> dz = mg_smooth<TA>(v.mi, v.NN, tid, mk2<TA>(rr.x - kz.x, rr.y - kz.y), om);
-      v.t[tid] = mk2<TA>(z.x + dz.x, z.y + dz.y);
+    {  // post-smoothing t = z + omega M^-1 (r - K z), T lanes per node
+      const int T = mg_lanes(v.NN), node = tid / T, sub = tid % T;
+      const bool on = node < v.NN;
+      const int nd = on ? node : 0, ni = nd % v.n, nj = nd / v.n;
+      vec2_t<TA> kz = group_sum<TA>(mg_apply_part<TA>(v, v.z, ni, nj, on ? sub : 9, T), T);
+      if (on && sub == 0) {
+        if (pinned2(ni, nj, v.bc)) kz = mk2<TA>(TA(0), TA(0));
+        const vec2_t<TA> rr = v.r[nd], z = v.z[nd];
+        const vec2_t<TA> dz = mg_smooth<TA>(v.mi, v.NN, nd, mk2<TA>(rr.x - kz.x, rr.y - kz.y), om);
+        v.t[nd] = mk2<TA>(z.x + dz.x, z.y + dz.y);
+      }
     }
     __syncthreads();
   }
@@ -1434,8 +1472,9 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       // ones (the fine level is always the current tangent).  The V-cycle stays symmetric; it stays
       // positive definite while the kept Galerkin operators are and the damped smoother still
       // contracts at the current tangent, true for nearby tangents but not guaranteed under large
-      // stretch and contrast, so a PCG that breaks down or hits its cap with kept levels is run
-      // once more with levels rebuilt from the current element tangents.
+      // stretch and contrast, so a PCG that breaks down, hits its cap or sees negative curvature
+      // (which an indefinite V-cycle can fake) with kept levels is run once more with levels
+      // rebuilt from the current element tangents.
       // (The retry rebuilds the whole tangent: the coarse build must not run while the fine
       // stencil occupies the registers, and one call site of each keeps the code from spilling.)
       const bool reuse = kMG && mg.levels && a.mg_reuse && it > 0;
@@ -1449,7 +1488,9 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
           build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb, mg, !reuse || attempt > 0);
         }
         cg_total += pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redD, &pst, true);
-        if (!(reuse && attempt == 0 && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap))) break;
+        if (!(reuse && attempt == 0 &&
+              (pst == kStatusPcgBreakdown || pst == kStatusPcgCap || pst == kStatusNegCurv)))
+          break;
         pst = kStatusOk;
         __syncthreads();
       }

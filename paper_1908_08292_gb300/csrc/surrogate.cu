@@ -281,3 +281,37 @@ extern "C" int fehmm_surrogate_targets(const fehmm_surrogate_params* sp, const d
                                                                     ty, tg);
   return cudaGetLastError() == cudaSuccess ? FEHMM_OK : FEHMM_ERR_CUDA;
 }
+
+// Base law of the surrogate from the small-strain homogenised tangent (host set-up arithmetic on
+// 81 numbers; see include/fehmm.h).
+extern "C" int fehmm_surrogate_base_law(const double* A0, fehmm_surrogate_params* sp) {
+  if (!A0 || !sp) return FEHMM_ERR_ARG;
+  double S[81];  // minor-symmetric part
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l)
+          S[((i * 3 + j) * 3 + k) * 3 + l] =
+              0.25 * (A0[((i * 3 + j) * 3 + k) * 3 + l] + A0[((j * 3 + i) * 3 + k) * 3 + l] +
+                      A0[((i * 3 + j) * 3 + l) * 3 + k] + A0[((j * 3 + i) * 3 + l) * 3 + k]);
+  double iijj = 0.0, ijij = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      iijj += S[((i * 3 + i) * 3 + j) * 3 + j];
+      ijij += S[((i * 3 + j) * 3 + i) * 3 + j];
+    }
+  const double K = iijj / 9.0, mu = (ijij - iijj / 3.0) / 10.0, lam = K - 2.0 * mu / 3.0;
+  if (!(mu > 0.0) || !(lam + 2.0 * mu / 3.0 > 0.0)) return FEHMM_ERR_ARG;
+  const int I6[6] = {0, 1, 2, 1, 0, 0}, J6[6] = {0, 1, 2, 2, 2, 1};
+  const double r2 = 1.4142135623730951;
+  for (int p = 0; p < 6; ++p)
+    for (int q = 0; q < 6; ++q) {
+      const int i = I6[p], j = J6[p], k = I6[q], l = J6[q];
+      const double iso = lam * (i == j) * (k == l) + mu * ((i == k) * (j == l) + (i == l) * (j == k));
+      const double wp = p < 3 ? 1.0 : r2, wq = q < 3 ? 1.0 : r2;
+      sp->Ca[6 * p + q] = wp * wq * (S[((i * 3 + j) * 3 + k) * 3 + l] - iso);
+    }
+  sp->lam0 = lam;
+  sp->mu0 = mu;
+  return FEHMM_OK;
+}

@@ -20,8 +20,6 @@ import numpy as np
 from . import Context, FehmmError, _check, _dev, _stream, lib
 
 WIDTH, N_IN, N_INP = 128, 6, 8
-SQ2 = math.sqrt(2.0)
-MANDEL = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
 
 
 def n_params() -> int:
@@ -192,17 +190,6 @@ def work_floats(n: int) -> int:
     return int(lib().fehmm_surrogate_work_floats(int(n)))
 
 
-def isotropic_projection(A):
-    """(lam, mu) of the isotropic part of a fourth-order tangent A[3,3,3,3]:
-    3K = A_iijj / 3, mu = (A_ijij - A_iijj / 3) / 10, lam = K - 2 mu / 3."""
-    A = np.asarray(A).reshape(3, 3, 3, 3)
-    iijj = np.einsum("iijj->", A)
-    ijij = np.einsum("ijij->", A)
-    K = iijj / 9.0
-    mu = (ijij - iijj / 3.0) / 10.0
-    return K - 2.0 * mu / 3.0, mu
-
-
 def surrogate_targets(sp: SurrogateParams, F, P, W, x, ty, tg, stream=None):
     import torch
     n = F.shape[0]
@@ -247,26 +234,17 @@ def rve_solve_batch(ctx, F, with_tangent=False, with_energy=True, stages=1):
     return P, A, W, st
 
 
-def mandel4(A):
-    """6x6 Mandel matrix of a fourth-order tensor with minor symmetries (order 11,22,33,23,13,12)."""
-    A = np.asarray(A).reshape(3, 3, 3, 3)
-    w = [1.0 if i == j else SQ2 for i, j in MANDEL]
-    return np.array([[A[i, j, k, l] * w[p] * w[q] for q, (k, l) in enumerate(MANDEL)] for p, (i, j) in enumerate(MANDEL)])
-
-
 def base_law(ctx_one):
-    """Base energy of the surrogate from the small-strain homogenised tangent A0 (F = I):
-    (lam0, mu0) its isotropic projection, Ca = Mandel(A0 - CC_iso(lam0, mu0)) the remainder.
-    Host arithmetic on the 81 entries of A0 (set-up)."""
+    """Base energy of the surrogate from the small-strain homogenised tangent A0 (an RVE solve at
+    F = I): (lam0, mu0) its isotropic projection and Ca the Mandel form of the remainder, both by
+    the library (fehmm_surrogate_base_law)."""
     import torch
     F = torch.eye(3, dtype=torch.float64, device="cuda").reshape(1, 9).repeat(ctx_one.n_qp, 1).contiguous()
     P, A, W, st = rve_solve_batch(ctx_one, F, with_tangent=True, with_energy=False)
-    A0 = A[0].cpu().numpy().reshape(3, 3, 3, 3)
-    A0 = 0.25 * (A0 + A0.transpose(1, 0, 2, 3) + A0.transpose(0, 1, 3, 2) + A0.transpose(1, 0, 3, 2))
-    lam0, mu0 = isotropic_projection(A0)
-    I = np.eye(3)
-    iso = lam0 * np.einsum("ij,kl->ijkl", I, I) + mu0 * (np.einsum("ik,jl->ijkl", I, I) + np.einsum("il,jk->ijkl", I, I))
-    return lam0, mu0, mandel4(A0 - iso)
+    A0 = np.ascontiguousarray(A[0].cpu().numpy(), dtype=np.float64)
+    sp = SurrogateParams()
+    _check(lib().fehmm_surrogate_base_law(A0.ctypes.data, ctypes.byref(sp)), "surrogate_base_law")
+    return sp.lam0, sp.mu0, np.array(sp.Ca[:]).reshape(6, 6)
 
 
 def generate(ctx, sp, U, chunk=None, stages=3, drop_failed=True):

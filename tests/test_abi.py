@@ -43,3 +43,36 @@ def test_default_options_and_argument_errors(L):
     assert L.fehmm_rve_solve(None, None, None, None, None, None, None, 0, None) == -1
     assert L.fehmm_status_str(-5).decode() == "unsupported configuration"
     assert L.fehmm_launch_count(None) == -1
+
+
+def test_surrogate_base_law_projection(L):
+    """fehmm_surrogate_base_law (host code, no GPU): an isotropic tangent gives back its Lame
+    constants and a zero remainder; a cubic one splits into its isotropic projection and a
+    remainder that restores it, in Mandel form."""
+    import numpy as np
+
+    import paper_1908_08292_gb300 as fe  # noqa: F401  (loads the signatures)
+    from paper_1908_08292_gb300.surrogate import SurrogateParams
+    I = np.eye(3)
+    II = np.einsum("ij,kl->ijkl", I, I)
+    Isym = np.einsum("ik,jl->ijkl", I, I) + np.einsum("il,jk->ijkl", I, I)
+    sp = SurrogateParams()
+    A = np.ascontiguousarray((1.7 * II + 0.9 * Isym).reshape(-1))
+    assert L.fehmm_surrogate_base_law(A.ctypes.data, ctypes.byref(sp)) == 0
+    assert abs(sp.lam0 - 1.7) < 1e-13 and abs(sp.mu0 - 0.9) < 1e-13
+    assert np.abs(np.array(sp.Ca[:])).max() < 1e-13
+    # cubic: extra stiffness c on the axial components only
+    cub = np.zeros((3, 3, 3, 3))
+    for i in range(3):
+        cub[i, i, i, i] = 0.6
+    A = 1.7 * II + 0.9 * Isym + cub
+    assert L.fehmm_surrogate_base_law(np.ascontiguousarray(A.reshape(-1)).ctypes.data, ctypes.byref(sp)) == 0
+    iso = sp.lam0 * II + sp.mu0 * Isym
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    w = [1.0, 1.0, 1.0] + [np.sqrt(2.0)] * 3
+    M = np.array([[(A - iso)[i, j, k, l] * w[p] * w[q] for q, (k, l) in enumerate(pairs)]
+                  for p, (i, j) in enumerate(pairs)])
+    np.testing.assert_allclose(np.array(sp.Ca[:]).reshape(6, 6), M, atol=1e-13)
+    # the projection removes the isotropic content: the remainder has no bulk or shear trace
+    R = A - iso
+    assert abs(np.einsum("iijj->", R)) < 1e-12 and abs(np.einsum("ijij->", R)) < 1e-12
