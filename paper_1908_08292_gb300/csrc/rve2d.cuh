@@ -674,39 +674,20 @@ __device__ __forceinline__ void mg_coarse_element(const TA* kf, int nf, int E, T
 __device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 __device__ __forceinline__ int wrap_inc(int i, int n) { return i == n - 1 ? 0 : i + 1; }
 
-// The share of y = K_l z at node (i, j) from the neighbour blocks nb = sub, sub + T, ... (a group
-// of T lanes computes one node; group_sum adds the shares).  Used on the coarse levels, where
-// a level has fewer nodes than the block has threads.
+// y = K_l z at node v = (i, j) of a coarse level (zero at the pinned node).
 template <typename TA>
-__device__ __forceinline__ vec2_t<TA> mg_apply_part(const MgLevel<TA>& L, const vec2_t<TA>* z, int i, int j, int sub,
-                                                    int T) {
+__device__ __forceinline__ vec2_t<TA> mg_apply(const MgLevel<TA>& L, const vec2_t<TA>* z, int i, int j) {
   const int n = L.n, v = i + n * j;
   const int cols[3] = {wrap_dec(i, n), i, wrap_inc(i, n)};
   const int rows[3] = {wrap_dec(j, n) * n, j * n, wrap_inc(j, n) * n};
   TA yx = TA(0), yy = TA(0);
-  for (int nb = sub; nb < 9; nb += T) {
+#pragma unroll
+  for (int nb = 0; nb < 9; ++nb) {
     const vec2_t<TA> zn = z[rows[nb / 3] + cols[nb % 3]];
     yx += L.st[(size_t)(nb * 4 + 0) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 1) * L.NN + v] * zn.y;
     yy += L.st[(size_t)(nb * 4 + 2) * L.NN + v] * zn.x + L.st[(size_t)(nb * 4 + 3) * L.NN + v] * zn.y;
   }
-  return mk2<TA>(yx, yy);
-}
-
-// Sum over aligned groups of T lanes (T a power of two dividing 32); all lanes must call it.
-template <typename TA>
-__device__ __forceinline__ vec2_t<TA> group_sum(vec2_t<TA> a, int T) {
-  for (int o = T >> 1; o > 0; o >>= 1) {
-    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
-    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
-  }
-  return a;
-}
-
-// Lanes per node for a coarse level of NN nodes: up to 8, as many as the block's threads allow.
-__device__ __forceinline__ int mg_lanes(int NN) {
-  int T = 1;
-  while (T < 8 && 2 * T * NN <= (int)blockDim.x) T *= 2;
-  return T;
+  return pinned2(i, j, L.bc) ? mk2<TA>(TA(0), TA(0)) : mk2<TA>(yx, yy);
 }
 
 template <typename TA>
@@ -890,16 +871,9 @@ __device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
   const TA om = mg.omega;
   for (int l = 1; l < mg.levels; ++l) {  // descend: residual, restrict (+ next pre-smoothing)
     const MgLevel<TA> v = mg.level(l);
-    {  // t = r - K z, T lanes per node
-      const int T = mg_lanes(v.NN), node = tid / T, sub = tid % T;
-      const bool on = node < v.NN;
-      const int nd = on ? node : 0, i = nd % v.n, j = nd / v.n;
-      vec2_t<TA> kz = group_sum<TA>(mg_apply_part<TA>(v, v.z, i, j, on ? sub : 9, T), T);
-      if (on && sub == 0) {
-        if (pinned2(i, j, v.bc)) kz = mk2<TA>(TA(0), TA(0));
-        const vec2_t<TA> rr = v.r[nd];
-        v.t[nd] = mk2<TA>(rr.x - kz.x, rr.y - kz.y);
-      }
+    if (tid < v.NN) {
+      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, tid % v.n, tid / v.n), rr = v.r[tid];
+      v.t[tid] = mk2<TA>(rr.x - kz.x, rr.y - kz.y);
     }
     __syncthreads();
     if (tid < mg.level(l + 1).NN) mg_restrict_smooth<TA>(mg, l + 1, v.t, v.n, tid);
@@ -928,17 +902,10 @@ __device__ void mg_coarse_cycle(const MgCtx<TA>& mg) {
       v.z[tid] = mk2<TA>(zo.x + zp.x, zo.y + zp.y);
     }
     __syncthreads();
-    {  // post-smoothing t = z + omega M^-1 (r - K z), T lanes per node
-      const int T = mg_lanes(v.NN), node = tid / T, sub = tid % T;
-      const bool on = node < v.NN;
-      const int nd = on ? node : 0, ni = nd % v.n, nj = nd / v.n;
-      vec2_t<TA> kz = group_sum<TA>(mg_apply_part<TA>(v, v.z, ni, nj, on ? sub : 9, T), T);
-      if (on && sub == 0) {
-        if (pinned2(ni, nj, v.bc)) kz = mk2<TA>(TA(0), TA(0));
-        const vec2_t<TA> rr = v.r[nd], z = v.z[nd];
-        const vec2_t<TA> dz = mg_smooth<TA>(v.mi, v.NN, nd, mk2<TA>(rr.x - kz.x, rr.y - kz.y), om);
-        v.t[nd] = mk2<TA>(z.x + dz.x, z.y + dz.y);
-      }
+    if (tid < v.NN) {
+      const vec2_t<TA> kz = mg_apply<TA>(v, v.z, i, j), rr = v.r[tid], z = v.z[tid];
+      const vec2_t<TA> dz = mg_smooth<TA>(v.mi, v.NN, tid, mk2<TA>(rr.x - kz.x, rr.y - kz.y), om);
+      v.t[tid] = mk2<TA>(z.x + dz.x, z.y + dz.y);
     }
     __syncthreads();
   }
@@ -1082,10 +1049,11 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
   TA gamma = (TA)gd, delta = (TA)dd;
   const double gamma0 = gd;
   const double stop = (double)rtol * (double)rtol * (warm ? gref : gamma0);
-  // a non-finite preconditioned residual (e.g. a multigrid coarse inverse of an indefinite
-  // tangent) is a breakdown, not a converged zero correction
-  if (!isfinite(gamma0)) *status = kStatusPcgBreakdown;
-  if (gamma0 > 0.0 && isfinite(gamma0) && !(warm && gamma0 <= stop)) {
+  // a non-finite or negative preconditioned residual norm r^T M^-1 r (a multigrid coarse inverse of
+  // an indefinite tangent, or a V-cycle that is not positive definite) is a breakdown, not a
+  // converged zero correction
+  if (!isfinite(gamma0) || gamma0 < 0.0 || (warm && !(gref >= 0.0))) *status = kStatusPcgBreakdown;
+  if (*status == kStatusOk && gamma0 > 0.0 && !(warm && gamma0 <= stop)) {
     if (!(dd > 0.0)) {
       if (truncate && delta < TA(0)) {
         const TA a0 = cg_div<TA>(gamma, -delta);
@@ -1116,6 +1084,10 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
                             w[0] * u[0] + w[1] * u[1] + w[2] * u[2] + w[3] * u[3], red, gnd, dnd);
         const TA gn = (TA)gnd, dn = (TA)dnd;
         ++it;
+        if (!(gnd >= 0.0)) {  // preconditioner not positive definite (or non-finite)
+          *status = kStatusPcgBreakdown;
+          break;
+        }
         if (gnd <= stop) break;
         const TA beta = cg_div<TA>(gn, gamma);
         const TA den = dn - beta * cg_div<TA>(gn, alpha);  // p_new^T K p_new

@@ -36,7 +36,7 @@
 namespace fehmm {
 namespace {
 
-constexpr int kThreads3D = 384;
+constexpr int kThreads3D = 512;
 // Gauss-point data per law: neo-Hookean Fit (9), hb, gm, padding (12); St. Venant-Kirchhoff F (9),
 // S (6: 00, 01, 02, 11, 12, 22), padding (16).  Scratch is sized for the larger.
 constexpr int kLawNH = 0, kLawSVK = 1;
@@ -339,20 +339,10 @@ __device__ inline Scratch3<TA> scratch3_layout(unsigned char* base, int NN) {
   return s;
 }
 
-// Mixed precision recomputes the Gauss-point data inside the tangent apply from an FP32 copy of
-// the fluctuation in shared memory (about 100 extra FP32 flops per Gauss point instead of
-// streaming 12 stored values per Gauss point from the block's scratch, which for 152 blocks of
-// 16^3 RVEs does not fit in L2).  The stored data are still written when the multigrid's first
-// coarse level is built from them.  FP64 mode (the parity mode) keeps the stored data.
-template <typename TA>
-__host__ __device__ constexpr bool recompute3() { return sizeof(TA) == 4; }
-
-// shared memory: vin [3][NN], vout [3][NN], (mixed) w32 [3][NN] (TA), reductions, lame, misc
-template <typename TA>
-__host__ __device__ inline size_t smem3_vecs() { return recompute3<TA>() ? 9 : 6; }
+// shared memory: vin [3][NN], vout [3][NN] (TA), reductions, lame, misc
 template <typename TA>
 __host__ __device__ inline size_t smem3_bytes(int NN) {
-  return sizeof(TA) * smem3_vecs<TA>() * (size_t)NN + sizeof(double) * (2 * 512 + 2 * kMaxPhase + 128);
+  return sizeof(TA) * 6 * (size_t)NN + sizeof(double) * (2 * 512 + 2 * kMaxPhase + 128);
 }
 
 template <typename T>
@@ -418,7 +408,6 @@ struct Ctx3 {
   Scratch3<TA> sc;
   TA* vin;   // shared [3][NN]
   TA* vout;  // shared [3][NN]
-  TA* w32;   // shared [3][NN]: the fluctuation in TA (mixed mode), refreshed by every tangent3
   double* red;  // shared 2*512
   int bc;       // 0 periodic, 1 KUBC (pinned3)
   double Fb[9];
@@ -543,18 +532,10 @@ __device__ __forceinline__ void gather_R(const Ctx3<TA>& c, int v, double (&R)[3
 // Gauss-point data and nodal diagonal blocks (accumulated in shared memory vin|vout as
 // [6][NN]); optional FP64 accumulation of <A> (45 symmetric entries) for the transfer.
 template <typename TA, int LAW, bool withA>
-__device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double* Asum /*[45] per thread, withA only*/,
-                                      bool store = true /* write the Gauss-point data (needed by a coarse build) */) {
+__device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double* Asum /*[45] per thread, withA only*/) {
   const int n = c.g.n, NN = c.g.NN;
   TA* diag = c.vin;  // [6][NN] spans vin and vout
   for (int v = threadIdx.x; v < 6 * NN; v += blockDim.x) diag[v] = TA(0);
-  if constexpr (recompute3<TA>()) {
-    for (int v = threadIdx.x; v < NN; v += blockDim.x)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) c.w32[d * NN + v] = (TA)w[3 * v + d];
-  } else {
-    store = true;
-  }
   __syncthreads();
   const TA ih = (TA)n, wq = TA(0.125) / (ih * ih * ih);
   for (int e = threadIdx.x; e < c.NE; e += blockDim.x) {
@@ -587,7 +568,7 @@ __device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double
         qv[9] = m.hb;
         qv[10] = m.gm;
         qv[11] = TA(0);
-        if (store) store_qp<12>(c.sc.qpd, c.NE, q, e, qv);
+        store_qp<12>(c.sc.qpd, c.NE, q, e, qv);
         // diagonal blocks: K_aa,ik = wq [mu |g_a|^2 d_ik + (gm - hb) v_a,i v_a,k], v_a = Fit g_a
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
@@ -627,7 +608,7 @@ __device__ __noinline__ void tangent3(const Ctx3<TA>& c, const double* w, double
 #pragma unroll
         for (int k = 0; k < 6; ++k) qv[9 + k] = S6[k];
         qv[15] = TA(0);
-        if (store) store_qp<16>(c.sc.qpd, c.NE, q, e, qv);
+        store_qp<16>(c.sc.qpd, c.NE, q, e, qv);
         TA b6[6];  // b = F F^T (00, 01, 02, 11, 12, 22)
         {
           const int I6[6] = {0, 0, 0, 1, 1, 2}, J6[6] = {0, 1, 2, 1, 2, 2};
@@ -718,22 +699,13 @@ __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) u[a][i] = c.vin[i * NN + nd[a]];
     }
-    TA uw[8][3];  // the fluctuation at the corners (recompute mode)
-    if constexpr (recompute3<TA>()) {
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) uw[a][i] = c.w32[i * NN + nd[a]];
-    }
     const int ph = c.phase[e];
-    const TA mu = (TA)c.lame[2 * ph + 1], lam = (TA)c.lame[2 * ph];
+    const TA mu = (TA)c.lame[2 * ph + 1];
     TA y[8][3];
 #pragma unroll
     for (int a = 0; a < 8; ++a) y[a][0] = y[a][1] = y[a][2] = TA(0);
-    // stored data: the Gauss-point loop is unrolled so the shape-function weights fold to
-    // constants; recompute mode: a rolled loop (the fluctuation's corner values stay live too)
-#pragma unroll(recompute3<TA>() ? 1 : 8)
-    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {  // fully unrolled: the shape-function weights fold to constants
       const TA s = (TA)g01(q & 1), t = (TA)g01((q >> 1) & 1), r = (TA)g01(q >> 2);
       TA dF[9];
       if (mode == 0) {
@@ -746,27 +718,14 @@ __device__ __noinline__ void apply3(const Ctx3<TA>& c, int mode, int cidx) {
         for (int k = 0; k < 9; ++k) dF[k] = k == cidx ? TA(1) : TA(0);
       }
       TA dP[9];
-      if constexpr (recompute3<TA>()) {  // F = Fbar + Grad w at this Gauss point
-        TA Gw[9], F[9];
-        nat_grad(uw, s, t, r, Gw);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) F[k] = (TA)c.Fb[k] + ih * Gw[k];
-        if constexpr (LAW == kLawNH) {
-          const NH3<TA> m = nh3_eval(F, lam, mu);
-          tangent_action(m.Fit, m.hb, m.gm, mu, dF, dP);
-        } else {
-          TA S6[6];
-          svk3_S(F, lam, mu, S6);
-          svk_tangent_action(F, S6, lam, mu, dF, dP);
-        }
-      } else if constexpr (LAW == kLawNH) {
+      if constexpr (LAW == kLawNH) {
         TA qv[12];
         load_qp<12>(c.sc.qpd, c.NE, q, e, qv);
         tangent_action(qv, qv[9], qv[10], mu, dF, dP);
       } else {
         TA qv[16];
         load_qp<16>(c.sc.qpd, c.NE, q, e, qv);
-        svk_tangent_action(qv, qv + 9, lam, mu, dF, dP);
+        svk_tangent_action(qv, qv + 9, (TA)c.lame[2 * ph], mu, dF, dP);
       }
       nat_scatter(dP, cw, s, t, r, y);
     }
@@ -1282,14 +1241,16 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
   TA gamma = (TA)gd, delta = (TA)dd;
   const double gamma0 = gd;
   const double stop = (double)rtol * (double)rtol * (warm ? gref : gamma0);
-  if (warm && gamma0 <= stop) {  // the start value already meets the tolerance
+  // a non-finite or negative preconditioned residual norm r^T M^-1 r (the preconditioner is not
+  // positive definite) is a breakdown
+  if (!isfinite(gamma0) || gamma0 < 0.0 || (warm && !(gref >= 0.0))) {
+    *status = kStatusPcgBreakdown;
     __syncthreads();
     return it;
   }
-  if (!isfinite(gamma0)) {  // non-finite preconditioned residual: a breakdown
-    *status = kStatusPcgBreakdown;
+  if (warm && gamma0 <= stop) {  // the start value already meets the tolerance
     __syncthreads();
-    return 0;
+    return it;
   }
   if (!(gamma0 > 0.0)) return 0;
   if (!(dd > 0.0)) {
@@ -1324,6 +1285,10 @@ __device__ int pcg3(const Ctx3<TA>& c, TA rtol, int max_it, bool truncate, int* 
     dots(gnd, dnd);
     const TA gn = (TA)gnd, dn = (TA)dnd;
     ++it;
+    if (!(gnd >= 0.0)) {  // preconditioner not positive definite (or non-finite)
+      *status = kStatusPcgBreakdown;
+      break;
+    }
     if (gnd <= stop) break;
     beta = div3(gn, gamma);
     const TA den = dn - beta * div3(gn, alpha);
@@ -1355,8 +1320,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
   c.phase = a.phase + a.rve_phase_off[rv];
   c.vin = reinterpret_cast<TA*>(smem);
   c.vout = c.vin + 3 * NN;
-  c.w32 = recompute3<TA>() ? c.vout + 3 * NN : nullptr;
-  c.red = reinterpret_cast<double*>(smem + sizeof(TA) * smem3_vecs<TA>() * (size_t)a.nn_max);
+  c.red = reinterpret_cast<double*>(smem + sizeof(TA) * 6 * (size_t)a.nn_max);
   double* lame_s = c.red + 2 * 512;
   double* misc = lame_s + 2 * kMaxPhase;
   c.lame = lame_s;
@@ -1434,8 +1398,7 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
         status = kStatusNewtonCap;
         break;
       }
-      const bool reused = c.mg.levels && it > 0 && a.mg_reuse;
-      tangent3<TA, LAW, false>(c, w, nullptr, !reused);  // Gauss-point data only for a coarse build
+      tangent3<TA, LAW, false>(c, w, nullptr);
       // The coarse levels are built on the first Newton iteration of a solve (or continuation
       // stage) and reused by the later ones, with the current fine operator, smoother and
       // residual.  The V-cycle stays symmetric; it stays positive definite as long as the reused
@@ -1446,13 +1409,13 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       // with levels rebuilt at the current tangent (its right-hand side
       // is kept in the transfer area, unused during Newton).  The tangent transfer always
       // rebuilds them at the converged state.
+      const bool reused = c.mg.levels && it > 0 && a.mg_reuse;
       if (c.mg.levels && !reused) mg3_build<TA, LAW>(c);
       if (reused)
         for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.L[v] = c.sc.r[v];
       int pst = kStatusOk;
       cg_total += pcg3<TA, LAW>(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
       if (reused && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap || pst == kStatusNegCurv)) {
-        tangent3<TA, LAW, false>(c, w, nullptr, true);
         mg3_build<TA, LAW>(c);
         for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.r[v] = c.sc.L[v];
         __syncthreads();
