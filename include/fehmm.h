@@ -127,7 +127,9 @@ typedef struct {
   double mg_omega;      /* damping of the multigrid's block-Jacobi smoother, in (0, 1); the
                            V-cycle is a positive definite preconditioner only while omega <
                            2 / lambda_max(D^-1 K) (about 0.86 for Q1, 0.67 for Hex8 elasticity).
-                           Default 0.7 (2D), 0.6 (3D). */
+                           Default 0.7 (2D), 0.6 (3D).  A PCG that breaks down (negative
+                           r^T M^-1 r: the V-cycle is not positive definite at that tangent) or
+                           hits its cap is rerun with half the damping, down to omega / 8. */
   int mg_reuse;         /* 3D multigrid: 1 (default) builds the coarse levels at the first Newton
                            iteration of a solve and reuses them in the later ones; 0 rebuilds
                            them at every Newton iteration */

@@ -108,7 +108,7 @@ template <typename TA>
 struct Smem2D {
   double2* w;        // [NN] fluctuation (FP64)
   float2* w32;       // [NN] FP32 copy (mixed mode only)
-  vec2_t<TA>* p;     // [NN] PCG exchange vector (u = M^-1 r)
+  vec2_t<TA>* p;     // [2][NN] PCG exchange vector (u = M^-1 r), two alternating buffers
   vec2_t<TA>* x;     // [NN] PCG solution (owned nodes written by their thread)
   unsigned char* stage;  // element forces / element tangents / condensation solutions
   double* red;       // 2 x 512 doubles of reduction buffers
@@ -127,7 +127,7 @@ __host__ __device__ inline size_t smem2d_layout(int NN, Smem2D<TA>* s, unsigned 
   };
   size_t o_w = take(sizeof(double2) * NN);
   size_t o_w32 = REG ? take(sizeof(float2) * NN) : 0;
-  size_t o_p = take(sizeof(vec2_t<TA>) * NN);
+  size_t o_p = take(2 * sizeof(vec2_t<TA>) * NN);
   size_t o_x = take(sizeof(vec2_t<TA>) * NN);
   size_t stage_bytes = sizeof(double) * 8 * NN;                               // element forces
   // condensation solutions X[4][NN] and right-hand sides L[4][NN]; in mixed mode followed by
@@ -956,14 +956,19 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
       xs[o.node[1]] = mk2<TA>(TA(0), TA(0));
     }
   }
+  // The exchange alternates between two buffers: the barrier of exchange k + 1 orders every read of
+  // exchange k before the writes of exchange k + 2, so no barrier is needed after the reads.
+  int pb = 0;
   auto exchange_apply = [&]() {  // w = K u
+    vec2_t<TA>* pbuf = ps + (pb ? o.NN : 0);
+    pb ^= 1;
     if (o.active) {
-      ps[o.node[0]] = mk2<TA>(u[0], u[1]);
-      ps[o.node[1]] = mk2<TA>(u[2], u[3]);
+      pbuf[o.node[0]] = mk2<TA>(u[0], u[1]);
+      pbuf[o.node[1]] = mk2<TA>(u[2], u[3]);
     }
     __syncthreads();
     if (o.active) {
-      apply_pair<TA, REG>(S, o, ps, u, w);
+      apply_pair<TA, REG>(S, o, pbuf, u, w);
       if (o.pin[0]) w[0] = w[1] = TA(0);  // pinned nodes
       if (o.pin[1]) w[2] = w[3] = TA(0);
     } else {
@@ -1008,10 +1013,9 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
         u[2 * q + 1] += zp.y;
       }
     }
-    exchange_apply();  // w = K u (every read of ps by the first apply ended before the barriers)
+    exchange_apply();  // w = K u
     const TA t[4] = {r[0] - w[0], r[1] - w[1], r[2] - w[2], r[3] - w[3]};
     jacobi(t, om);     // post-smoothing
-    __syncthreads();   // every read of ps done before the caller's exchange
   };
   *status = kStatusOk;
   double gref = -1.0;  // stopping reference b^T M^-1 b of a warm start
@@ -1036,7 +1040,6 @@ __device__ __forceinline__ int pcg_pair(const Stencil<TA, REG>& S, const Own2D& 
     exchange_apply();
 #pragma unroll
     for (int k = 0; k < 4; ++k) r[k] -= w[k];
-    __syncthreads();  // every read of ps done before the next exchange
     it = 1;
   }
   precond();
@@ -1449,23 +1452,33 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
       // rebuilt from the current element tangents.
       // (The retry rebuilds the whole tangent: the coarse build must not run while the fine
       // stencil occupies the registers, and one call site of each keeps the code from spilling.)
-      const bool reuse = kMG && mg.levels && a.mg_reuse && it > 0;
+      // A V-cycle whose fresh levels still break down (its damped smoother no longer contracts at
+      // this tangent, e.g. St. Venant-Kirchhoff under compression) is retried with half the
+      // damping, down to omega / 8.
+      bool reuse = kMG && mg.levels && a.mg_reuse && it > 0;
       TA b[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) b[k] = (TA)(-R[k]);
       int pst = kStatusOk;
+      const TA omega0 = mg.omega;
       for (int attempt = 0;; ++attempt) {
         {
           const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
-          build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb, mg, !reuse || attempt > 0);
+          build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, false, Lb, mg, !reuse);
         }
         cg_total += pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, sm.x, (TA)a.cg_rtol, a.max_cg, sm.p, redD, &pst, true);
-        if (!(reuse && attempt == 0 &&
-              (pst == kStatusPcgBreakdown || pst == kStatusPcgCap || pst == kStatusNegCurv)))
-          break;
-        pst = kStatusOk;
         __syncthreads();
+        if (reuse && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap || pst == kStatusNegCurv)) {
+          reuse = false;  // once more with levels of the current tangent
+        } else if (kMG && mg.levels && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap) &&
+                   mg.omega > TA(0.2) * omega0) {
+          mg.omega *= TA(0.5);
+        } else {
+          break;
+        }
+        pst = kStatusOk;
       }
+      mg.omega = omega0;
       if (pst == kStatusPcgBreakdown) {
         status = kStatusPcgBreakdown;
         break;
@@ -1544,6 +1557,7 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
     // kept solutions of this point's previous transfer solves ([4][NN] vec2, zero at first)
     const bool warm = a.X_in != nullptr;
     const vec2_t<TA>* X0 = warm ? reinterpret_cast<const vec2_t<TA>*>(a.X_in) + 2 * w_off : nullptr;
+    const TA omega0 = mg.omega;
     for (int c = 0; c < 4; ++c) {
       TA b[4] = {TA(0), TA(0), TA(0), TA(0)};
       if (o.active) {
@@ -1552,15 +1566,24 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
         b[1] = b0.y;
         b[2] = b1.x;
         b[3] = b1.y;
-        if (warm) {
+      }
+      int pst = kStatusOk, ci = 0;
+      for (;;) {  // as for the Newton corrections: a breakdown is retried with half the damping
+        if (warm && o.active) {
 #pragma unroll
           for (int s = 0; s < 2; ++s)
             X[c * NN + o.node[s]] = o.pin[s] ? mk2<TA>(TA(0), TA(0)) : X0[c * NN + o.node[s]];
         }
+        ci += pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, X + c * NN, (TA)a.cond_rtol, a.max_cond_cg, sm.p, redD, &pst,
+                                     false, warm);
+        __syncthreads();
+        if (!(kMG && mg.levels && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap) &&
+              mg.omega > TA(0.2) * omega0))
+          break;
+        mg.omega *= TA(0.5);
+        pst = kStatusOk;
       }
-      int pst = kStatusOk;
-      const int ci = pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, X + c * NN, (TA)a.cond_rtol, a.max_cond_cg, sm.p,
-                                            redD, &pst, false, warm);
+      mg.omega = omega0;
       cond_total += ci;
       cond_max = ci > cond_max ? ci : cond_max;
       if (pst != kStatusOk && status == kStatusOk) status = pst;

@@ -1409,19 +1409,30 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       // with levels rebuilt at the current tangent (its right-hand side
       // is kept in the transfer area, unused during Newton).  The tangent transfer always
       // rebuilds them at the converged state.
-      const bool reused = c.mg.levels && it > 0 && a.mg_reuse;
+      // A V-cycle whose fresh levels still break down (its damped smoother no longer contracts at
+      // this tangent) is retried with half the damping, down to omega / 8.
+      bool reused = c.mg.levels && it > 0 && a.mg_reuse;
       if (c.mg.levels && !reused) mg3_build<TA, LAW>(c);
-      if (reused)
+      if (c.mg.levels)
         for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.L[v] = c.sc.r[v];
       int pst = kStatusOk;
-      cg_total += pcg3<TA, LAW>(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
-      if (reused && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap || pst == kStatusNegCurv)) {
-        mg3_build<TA, LAW>(c);
+      const TA omega0 = c.mg.omega;
+      for (;;) {
+        cg_total += pcg3<TA, LAW>(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
+        if (reused && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap || pst == kStatusNegCurv)) {
+          mg3_build<TA, LAW>(c);
+          reused = false;
+        } else if (c.mg.levels && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap) &&
+                   c.mg.omega > TA(0.2) * omega0) {
+          c.mg.omega *= TA(0.5);
+        } else {
+          break;
+        }
         for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) c.sc.r[v] = c.sc.L[v];
         __syncthreads();
         pst = kStatusOk;
-        cg_total += pcg3<TA, LAW>(c, (TA)a.cg_rtol, a.max_cg, true, &pst);
       }
+      c.mg.omega = omega0;
       if (pst == kStatusPcgBreakdown) {
         status = kStatusPcgBreakdown;
         break;
@@ -1487,14 +1498,22 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
     const bool warm = a.X_in != nullptr;
     const TA* X0 = warm ? reinterpret_cast<const TA*>(a.X_in) + 9 * (size_t)a.qp_w_off[qp] : nullptr;
     TA* X1 = a.X_out ? reinterpret_cast<TA*>(a.X_out) + 9 * (size_t)a.qp_w_off[qp] : nullptr;
+    const TA omega0 = c.mg.omega;
     for (int cp = 0; cp < 9; ++cp) {
-      for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
-        c.sc.r[v] = -c.sc.L[(size_t)cp * 3 * NN + v];
-        if (warm) c.sc.x[v] = X0[(size_t)cp * 3 * NN + v];
+      int pst = kStatusOk, ci = 0;
+      for (;;) {  // as for the Newton corrections: a breakdown is retried with half the damping
+        for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) {
+          c.sc.r[v] = -c.sc.L[(size_t)cp * 3 * NN + v];
+          if (warm) c.sc.x[v] = X0[(size_t)cp * 3 * NN + v];
+        }
+        __syncthreads();
+        ci += pcg3<TA, LAW>(c, (TA)a.cond_rtol, a.max_cond_cg, false, &pst, warm);
+        if (!(c.mg.levels && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap) && c.mg.omega > TA(0.2) * omega0))
+          break;
+        c.mg.omega *= TA(0.5);
+        pst = kStatusOk;
       }
-      __syncthreads();
-      int pst = kStatusOk;
-      const int ci = pcg3<TA, LAW>(c, (TA)a.cond_rtol, a.max_cond_cg, false, &pst, warm);
+      c.mg.omega = omega0;
       if (X1)
         for (int v = threadIdx.x; v < 3 * NN; v += blockDim.x) X1[(size_t)cp * 3 * NN + v] = c.sc.x[v];
       cond_total += ci;
