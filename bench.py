@@ -1089,6 +1089,19 @@ def run_schemes(args):
                                "micro_newton_iters": int(sum(sum(r["micro_newton"]) for r in recs)),
                                "all_converged": bool(all(r["converged"] for r in recs)),
                                "macro_iters_per_step": [r["macro_iters"] for r in recs]}
+                # where the RVE time goes: the same load path once more, instrumented (eager): RVE
+                # kernel time and the PCG iterations of the Newton corrections vs the transfer
+                drv.close()
+                drv = LoadStepDriver(p, scheme=scheme, graphs=False, **opts)
+                drv.rve_events, drv.iter_log = [], []
+                for k in range(1, steps + 1):
+                    drv.load_step(k)
+                torch.cuda.synchronize()
+                its = [t.cpu().numpy() for t in drv.iter_log]
+                row[scheme]["rve_kernel_seconds"] = sum(a.elapsed_time(b) for a, b in drv.rve_events) / 1e3
+                row[scheme]["rve_passes"] = len(its)
+                row[scheme]["pcg_newton_per_rve"] = float(sum(i[:, 1].sum() for i in its) / p.n_qp)
+                row[scheme]["pcg_transfer_per_rve"] = float(sum(i[:, 2].sum() for i in its) / p.n_qp)
             except FehmmError as e:  # a scheme that fails on a case is a result, not a crash
                 row[scheme] = {"failed": str(e), "steps_done": len(recs)}
             finally:
