@@ -96,6 +96,32 @@ __device__ __forceinline__ void block_dot2_fp64(T a, T b, double* buf, double& s
   sb = buf[33];
 }
 
+// 1/J for the FP64 neo-Hookean stress of the residuals: the FP32 approximate reciprocal (rcp.approx, relative error
+// below 2^-22) refined by two Newton-Raphson steps x <- x + x (1 - J x) in FP64, each of which
+// squares the relative error (2^-44, then below FP64 rounding), so the result is within an ulp
+// or so of the rounded quotient.  J below FP32's normal range (a collapsed element) gives a
+// non-finite result, which the Newton loop treats like J <= 0.
+__device__ __forceinline__ double recip_fp64(double J) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"((float)J));
+  double x = (double)r;
+  double e = fma(-J, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-J, x, 1.0);
+  return fma(x, e, x);
+}
+
+// 1/J at the tangent's precision: FP32 through the hardware approximate reciprocal (about one
+// FP32 ulp, ample for an FP32 tangent), FP64 as a plain division.
+template <typename T>
+__device__ __forceinline__ T recip_T(T J) {
+  if constexpr (sizeof(T) == 4) {
+    return __fdividef(1.f, J);
+  } else {
+    return 1.0 / J;
+  }
+}
+
 // Lame constants from (E, nu), as in the paper's material table (Sec. 6).
 __host__ __device__ inline void lame_from_E_nu(double E, double nu, double& lam, double& mu) {
   lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
@@ -113,7 +139,7 @@ template <typename T>
 __device__ __forceinline__ NH2<T> nh2_eval(T F00, T F01, T F10, T F11, T lam, T mu) {
   NH2<T> r;
   r.J = F00 * F11 - F01 * F10;
-  const T iJ = T(1) / r.J;
+  const T iJ = recip_T(r.J);
   r.f00 = F11 * iJ;
   r.f01 = -F10 * iJ;
   r.f10 = -F01 * iJ;

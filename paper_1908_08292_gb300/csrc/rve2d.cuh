@@ -216,7 +216,7 @@ __device__ __forceinline__ T law2_P(T F00, T F01, T F10, T F11, T lam, T mu, T& 
     // P = mu F + hb F^-T with F^-T = cof(F) / J, i.e. P = mu F + c cof(F),
     // c = hb / J = lam J / 2 - (lam / 2 + mu) / J (cof(F) = [[F11, -F10], [-F01, F00]])
     const T J = F00 * F11 - F01 * F10;
-    const T c = fma(T(0.5) * lam, J, -(T(0.5) * lam + mu) / J);
+    const T c = fma(T(0.5) * lam, J, -(T(0.5) * lam + mu) * recip_T(J));
     P00 = fma(mu, F00, c * F11);
     P01 = fma(mu, F01, -c * F10);
     P10 = fma(mu, F10, -c * F01);
@@ -235,8 +235,35 @@ __device__ __forceinline__ T law2_P(T F00, T F01, T F10, T F11, T lam, T mu, T& 
 }
 
 // ------------------------------------------------------------------ residual (FP64)
+// FP64 first Piola-Kirchhoff stress at one Gauss point (the residual's law; same factored forms
+// as law2_P, with the reciprocal above in place of a division).
+template <int LAW>
+__device__ __forceinline__ double law2_P_fp64(double F00, double F01, double F10, double F11, double hl, double hk,
+                                              double lam, double mu, double& P00, double& P01, double& P10,
+                                              double& P11) {
+  if constexpr (LAW == kLawNH) {
+    // c = lam J / 2 - (lam / 2 + mu) / J with hl = lam / 2, hk = lam / 2 + mu
+    const double J = fma(F00, F11, -F01 * F10);
+    const double c = fma(hl, J, -hk * recip_fp64(J));
+    P00 = fma(mu, F00, c * F11);
+    P01 = fma(mu, F01, -c * F10);
+    P10 = fma(mu, F10, -c * F01);
+    P11 = fma(mu, F11, c * F00);
+    return J;
+  } else {
+    return law2_P<LAW, double>(F00, F01, F10, F11, lam, mu, P00, P01, P10, P11);
+  }
+}
+
 // Element e's nodal forces into stage[k][e] (k = 2*local_node + comp) and this thread's
 // contributions to sum wt P and to the J <= 0 flag.
+//
+// With natural coordinates (s, t) in [0,1]^2 the displacement gradient is bilinear: the first
+// column of F depends on t only, the second on s only.  The nodal forces are (wq / h) P G_a with
+// wq = h^2 / 4 and G_a the natural-coordinate shape gradients, i.e. sums of P's first column
+// weighted by (1 - t) or t and of its second column weighted by (1 - s) or s.  The stress is
+// therefore summed over the Gauss points of equal t (first column) or equal s (second column)
+// first, and the two Gauss abscissae g0 and g1 = 1 - g0 give both weights.
 template <int LAW>
 __device__ __forceinline__ void element_residual(int e, int n, const double2* w, const double* Fb,
                                                  double lam, double mu, double* stage_f, double (&Psum)[4],
@@ -248,47 +275,63 @@ __device__ __forceinline__ void element_residual(int e, int n, const double2* w,
   const double2 d30 = make_double2(w3.x - w0.x, w3.y - w0.y);
   const double2 e1 = make_double2((w2.x - w3.x) - d10.x, (w2.y - w3.y) - d10.y);
   const double2 e2 = make_double2((w2.x - w1.x) - d30.x, (w2.y - w1.y) - d30.y);
-  double Sa0x = 0, Sa0y = 0, Sa1x = 0, Sa1y = 0, Sb0x = 0, Sb0y = 0, Sb1x = 0, Sb1y = 0;
+  const double hl = 0.5 * lam, hk = hl + mu;
+  // F's first column at t = g0, g1; second column at s = g0, g1
+  double Fc0[2][2], Fc1[2][2];
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const double t = gauss01(g);
+    Fc0[g][0] = fma(ih, fma(t, e1.x, d10.x), Fb[0]);
+    Fc0[g][1] = fma(ih, fma(t, e1.y, d10.y), Fb[2]);
+    Fc1[g][0] = fma(ih, fma(t, e2.x, d30.x), Fb[1]);
+    Fc1[g][1] = fma(ih, fma(t, e2.y, d30.y), Fb[3]);
+  }
+  double q0x[2], q0y[2], q1x[2], q1y[2];  // P's first column summed over s (per t), second over t (per s)
   int nbad = 0;
 #pragma unroll
   for (int gy = 0; gy < 2; ++gy) {
-    const double t = gauss01(gy);
 #pragma unroll
     for (int gx = 0; gx < 2; ++gx) {
-      const double s = gauss01(gx);
-      const double F00 = fma(ih, fma(t, e1.x, d10.x), Fb[0]);
-      const double F10 = fma(ih, fma(t, e1.y, d10.y), Fb[2]);
-      const double F01 = fma(ih, fma(s, e2.x, d30.x), Fb[1]);
-      const double F11 = fma(ih, fma(s, e2.y, d30.y), Fb[3]);
       double P00, P01, P10, P11;
-      const double J = law2_P<LAW, double>(F00, F01, F10, F11, lam, mu, P00, P01, P10, P11);
+      const double J = law2_P_fp64<LAW>(Fc0[gy][0], Fc1[gx][0], Fc0[gy][1], Fc1[gx][1], hl, hk, lam, mu, P00, P01,
+                                        P10, P11);
       nbad += (J > 0.0) ? 0 : 1;
-      Psum[0] += P00;
-      Psum[1] += P01;
-      Psum[2] += P10;
-      Psum[3] += P11;
-      Sa0x = fma(1.0 - t, P00, Sa0x);
-      Sa0y = fma(1.0 - t, P10, Sa0y);
-      Sa1x = fma(t, P00, Sa1x);
-      Sa1y = fma(t, P10, Sa1y);
-      Sb0x = fma(1.0 - s, P01, Sb0x);
-      Sb0y = fma(1.0 - s, P11, Sb0y);
-      Sb1x = fma(s, P01, Sb1x);
-      Sb1y = fma(s, P11, Sb1y);
+      if (gx == 0) {
+        q0x[gy] = P00;
+        q0y[gy] = P10;
+      } else {
+        q0x[gy] += P00;
+        q0y[gy] += P10;
+      }
+      if (gy == 0) {
+        q1x[gx] = P01;
+        q1y[gx] = P11;
+      } else {
+        q1x[gx] += P01;
+        q1y[gx] += P11;
+      }
     }
   }
   if (nbad) bad += (double)nbad;
-  // R_a = (wq / h) P G_a with wq = h^2/4 and G_a the natural-coordinate gradients.
-  const double k = 0.25 / ih;
+  Psum[0] += q0x[0] + q0x[1];
+  Psum[1] += q1x[0] + q1x[1];
+  Psum[2] += q0y[0] + q0y[1];
+  Psum[3] += q1y[0] + q1y[1];
+  const double k = 0.25 / ih, kg0 = k * gauss01(0), kg1 = k * gauss01(1);
+  // weight 1 - t is g1 at t = g0 and g0 at t = g1
+  const double Sa0x = fma(kg1, q0x[0], kg0 * q0x[1]), Sa1x = fma(kg0, q0x[0], kg1 * q0x[1]);
+  const double Sa0y = fma(kg1, q0y[0], kg0 * q0y[1]), Sa1y = fma(kg0, q0y[0], kg1 * q0y[1]);
+  const double Sb0x = fma(kg1, q1x[0], kg0 * q1x[1]), Sb1x = fma(kg0, q1x[0], kg1 * q1x[1]);
+  const double Sb0y = fma(kg1, q1y[0], kg0 * q1y[1]), Sb1y = fma(kg0, q1y[0], kg1 * q1y[1]);
   const int NN = n * n;
-  stage_f[0 * NN + e] = k * (-Sa0x - Sb0x);
-  stage_f[1 * NN + e] = k * (-Sa0y - Sb0y);
-  stage_f[2 * NN + e] = k * (Sa0x - Sb1x);
-  stage_f[3 * NN + e] = k * (Sa0y - Sb1y);
-  stage_f[4 * NN + e] = k * (Sa1x + Sb1x);
-  stage_f[5 * NN + e] = k * (Sa1y + Sb1y);
-  stage_f[6 * NN + e] = k * (-Sa1x + Sb0x);
-  stage_f[7 * NN + e] = k * (-Sa1y + Sb0y);
+  stage_f[0 * NN + e] = -Sa0x - Sb0x;
+  stage_f[1 * NN + e] = -Sa0y - Sb0y;
+  stage_f[2 * NN + e] = Sa0x - Sb1x;
+  stage_f[3 * NN + e] = Sa0y - Sb1y;
+  stage_f[4 * NN + e] = Sa1x + Sb1x;
+  stage_f[5 * NN + e] = Sa1y + Sb1y;
+  stage_f[6 * NN + e] = -Sa1x + Sb0x;
+  stage_f[7 * NN + e] = -Sa1y + Sb0y;
 }
 
 // Psi summed over the element's Gauss points: neo-Hookean lam/4 (J^2-1) - (lam/2+mu) ln J +

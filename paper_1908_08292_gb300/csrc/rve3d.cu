@@ -109,7 +109,7 @@ __device__ __forceinline__ NH3<T> nh3_eval(const T (&F)[9], T lam, T mu) {
   const T c10 = F[2] * F[7] - F[1] * F[8], c11 = F[0] * F[8] - F[2] * F[6], c12 = F[1] * F[6] - F[0] * F[7];
   const T c20 = F[1] * F[5] - F[2] * F[4], c21 = F[2] * F[3] - F[0] * F[5], c22 = F[0] * F[4] - F[1] * F[3];
   r.J = F[0] * c00 + F[1] * c01 + F[2] * c02;
-  const T iJ = T(1) / r.J;
+  const T iJ = recip_T(r.J);
   r.Fit[0] = c00 * iJ;
   r.Fit[1] = c01 * iJ;
   r.Fit[2] = c02 * iJ;
@@ -440,10 +440,22 @@ __device__ __noinline__ void residual3(const Ctx3<TA>& c, const double* w, doubl
       for (int k = 0; k < 9; ++k) F[k] = c.Fb[k] + ih * G[k];
       double P[9];
       if constexpr (LAW == kLawNH) {
-        const NH3<double> m = nh3_eval(F, lam, mu);
-        bad += m.J > 0.0 ? 0.0 : 1.0;
+        // P = mu F + hb F^-T = mu F + (hb / J) cof(F), the reciprocal refined in FP64
+        double cof[9];
+        cof[0] = F[4] * F[8] - F[5] * F[7];
+        cof[1] = F[5] * F[6] - F[3] * F[8];
+        cof[2] = F[3] * F[7] - F[4] * F[6];
+        cof[3] = F[2] * F[7] - F[1] * F[8];
+        cof[4] = F[0] * F[8] - F[2] * F[6];
+        cof[5] = F[1] * F[6] - F[0] * F[7];
+        cof[6] = F[1] * F[5] - F[2] * F[4];
+        cof[7] = F[2] * F[3] - F[0] * F[5];
+        cof[8] = F[0] * F[4] - F[1] * F[3];
+        const double J = F[0] * cof[0] + F[1] * cof[1] + F[2] * cof[2];
+        bad += J > 0.0 ? 0.0 : 1.0;
+        const double c = (0.5 * lam * (J * J - 1.0) - mu) * recip_fp64(J);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) P[k] = mu * F[k] + m.hb * m.Fit[k];
+        for (int k = 0; k < 9; ++k) P[k] = fma(mu, F[k], c * cof[k]);
       } else {
         const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
                          F[2] * (F[3] * F[7] - F[4] * F[6]);
