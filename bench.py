@@ -42,7 +42,10 @@ MACRO_C3, N_STEPS_C3 = 8, 10
 
 # Algorithmic operation counts per unit of the 2D mixed kernel, counted from the kernel source
 # (an FMA counting 2).
-FP64_FLOP_PER_ELEMENT_RESIDUAL = 290.0   # F, J, F^-T, P and nodal forces at 4 Gauss points + gather
+# residual: differences of the corner fluctuations (12), F's two columns at the two Gauss
+# abscissae (32), per Gauss point J, the refined reciprocal (4 FMA), c and P (26 x 4), the stress
+# sums per Gauss line and their shape weights (43), nodal forces (8), gather and norm (10)
+FP64_FLOP_PER_ELEMENT_RESIDUAL = 211.0
 FP32_FLOP_PER_ELEMENT_TANGENT = 1350.0   # 8x8 element tangent at 4 Gauss points + stencil gather
 FP32_FLOP_PER_NODE_PCG_ITER = 100.0      # 9-block 2x2 stencil apply + vector updates + 2 dots
 FP32_FLOP_PER_ELEMENT_TRANSFER = 1500.0  # energy form of the tangent transfer (4 unit gradients)
@@ -53,7 +56,7 @@ FP32_FLOP_PER_ELEMENT_TRANSFER = 1500.0  # energy form of the tangent transfer (
 # node), coarse stencils and the coarsest Gauss-Jordan inverse (2 x 32^3 / 1024)
 FP32_FLOP_PER_NODE_MG_ITER = 238.0
 FP32_FLOP_PER_NODE_MG_BUILD = 570.0
-FP64_FLOP_PER_ELEMENT_RESIDUAL_3D = 2640.0   # Hex8: 8 Gauss points x (grad, F^-T, P, nodal forces)
+FP64_FLOP_PER_ELEMENT_RESIDUAL_3D = 2620.0   # Hex8: 8 Gauss points x (grad, cof(F), J, 1/J refined, P, nodal forces)
 FP32_FLOP_PER_ELEMENT_TANGENT_3D = 4200.0    # Gauss-point data + 3x3 diagonal blocks
 FP32_FLOP_PER_ELEMENT_APPLY_3D = 4000.0      # matrix-free apply: grad, dP = A:dF, nodal scatter
 FP32_FLOP_PER_NODE_PCG_ITER_3D = 30.0        # preconditioner + vector updates + dots
@@ -831,6 +834,12 @@ def run_c4(args):
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     _, _, _, Ph, Wh, dropped_h = su.generate(ctx, sp, Uh, drop_failed=False)
+    t_fit = 0.0
+    if args.c4_poly:  # the polynomial part first; the network learns what it leaves
+        t3 = time.perf_counter()
+        su.fit_poly(sp, x, ty, tg, max_degree=args.c4_poly)
+        torch.cuda.synchronize()
+        t_fit = time.perf_counter() - t3
     mlp = su.MLP(4096)
     mlp.set_params(su.init_params(7))
     torch.cuda.synchronize()
@@ -858,6 +867,16 @@ def run_c4(args):
     t_inf = time.perf_counter() - t2
     Psn, Phn = Ps.cpu().numpy(), Ph.cpu().numpy()
     e = su.stress_errors(Psn, Phn, 1e-3)
+    # the base law with the polynomial part alone (a zero network, no origin shift)
+    sp0 = su.SurrogateParams.from_buffer_copy(sp)
+    sp0.y0 = 0.0
+    for k in range(6):
+        sp0.g0[k] = 0.0
+    for k in range(36):
+        sp0.H0[k] = 0.0
+    m2.set_params(np.zeros(su.n_params(), dtype=np.float32))
+    su.surrogate_eval(m2, sp0, Fh, Ps, As, None, ins, work)
+    e_base = su.stress_errors(Ps.cpu().numpy(), Phn, 1e-3)
     rad = np.linalg.norm((Uh - np.eye(3)).reshape(n, 9), axis=1)
     bins = {}
     for lo, hi in ((0.0, 0.05), (0.05, 0.1), (0.1, 0.15), (0.15, 0.2), (0.2, 0.25), (0.25, 0.3001)):
@@ -890,11 +909,15 @@ def run_c4(args):
         "config": {"workload": f"fixed 12^3 two-inclusion RVE (ratio 10), {args.c4_samples} training U in "
                                f"|U-I|_F<=0.3, {args.c4_holdout} held-out, MLP 6-4x128 SiLU-1 BF16/FP32, AdamW "
                                f"batch 4096, {args.c4_epochs} epochs, Sobolev loss (W and S), origin shift to "
-                               f"{'third' if args.c4_hessian_origin else 'second'} order"},
+                               f"{'third' if args.c4_hessian_origin else 'second'} order"
+                               + (f", polynomial part of degree 3-{args.c4_poly} fitted first" if args.c4_poly else "")},
         "dropped_failed_solves": dropped + dropped_h, "base_law": {"lam0": lam0, "mu0": mu0},
         "train_seconds": t_train, "train_steps_per_s": steps / t_train, "loss_first_last": [hist[0], hist[-1]],
         "heldout_stress_err": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max()),
                                "median": float(np.median(e)), "n": int(n), "by_radius": bins},
+        "heldout_err_without_network": {"rms": float(np.sqrt((e_base ** 2).mean())), "max": float(e_base.max()),
+                                        "what": "base law" + (" + polynomial part" if args.c4_poly else "")},
+        "poly_fit_seconds": t_fit,
         "largest_radius_meeting_1e-4": r_star,
         "inference_points_per_s": n / t_inf, "oracle_verified": verified,
         "target_1e-4_met": bool(e.max() <= 1e-4),
@@ -903,7 +926,11 @@ def run_c4(args):
 
 def run_c5(args):
     """Config 5: one macro iteration of the surrogate-with-fallback path vs the plain GPU RVE path
-    from the same macro state (macro^3 Hex8, the fixed 12^3 RVE everywhere)."""
+    from the same macro state (macro^3 Hex8, the fixed 12^3 RVE everywhere).  The surrogate
+    iteration is timed in the state its own load path left (fallback points solve from whatever
+    fluctuations they last committed); the plain iteration is timed after every point's RVE has
+    been solved and committed at the previous load step's converged macro state, the warm start a
+    plain run of the load path would have."""
     import torch
 
     import synth
@@ -921,6 +948,8 @@ def run_c5(args):
         sp.set_Ca(Ca)
         gen = su.fixed_rve_context(4096)
         x, ty, tg, _, _, _ = su.generate(gen, sp, synth.stretch_ball(1004, args.c4_samples, 0.3))
+        if args.c4_poly:
+            su.fit_poly(sp, x, ty, tg, max_degree=args.c4_poly)
         mlp.set_params(su.init_params(7))
         su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096)
         sp.set_origin(mlp, hessian=args.c4_hessian_origin)
@@ -930,6 +959,7 @@ def run_c5(args):
     d = drv.drv
     for k in range(1, args.c5_step):  # reach the state of load step c5_step with the surrogate path
         d.load_step(k)
+    u_prev = d.u.clone()  # the converged macro state of load step c5_step - 1
     d.scale = args.c5_step / p.n_steps
     d.ctx.macro_apply_dirichlet(d.u, d.du, d.scale)
     n = p.n_qp
@@ -961,6 +991,12 @@ def run_c5(args):
     fallback = drv.fallback_count()
     audit = drv.audit_errors(1e-3) if args.c5_audit_stride else np.zeros(0)
     P_sur = d.P.clone()
+    # warm start of the plain path: RVE solves at the previous step's converged state, committed
+    F_prev = torch.zeros_like(d.F)
+    d.ctx.macro_qp_F(u_prev, F_prev)
+    d.ctx.rve_solve(F_prev, d.P, d.A, d.st, d.it, flags=SOLVE_FROM_COMMITTED)  # also keeps transfer solutions
+    primed_ok = int((d.st.cpu().numpy() <= 1).sum())
+    d.ctx.commit()
     t_p = timed(plain_iteration)
     st = d.st.cpu().numpy()
     e = su.stress_errors(P_sur.cpu().numpy(), d.P.cpu().numpy(), 1e-3)
@@ -973,10 +1009,77 @@ def run_c5(args):
                                f"step {args.c5_step}; trust radius {args.c5_radius}"},
         "plain_value": 1.0 / t_p, "gain": t_p / t_s, "seconds": {"surrogate": t_s, "plain": t_p},
         "fallback_points": fallback, "fallback_fraction": fallback / n, "plain_status_ok": int((st == 0).sum()),
+        "plain_warm_start": {"what": "every RVE solved (with its tangent transfer) and committed at load step "
+                                     "c5_step - 1's converged state before the plain iteration is timed",
+                             "points_ok": primed_ok},
         "audit": {"n": int(audit.size), "rms": float(np.sqrt((audit ** 2).mean())) if audit.size else None,
                   "max": float(audit.max()) if audit.size else None},
         "stress_err_vs_plain": {"rms": float(np.sqrt((e ** 2).mean())), "max": float(e.max())},
         "target_1e-4_met": bool(e.max() <= 1e-4),
+    }))
+
+
+def run_mlp(args):
+    """The surrogate network's kernels alone: AdamW training steps (loss, exact parameter gradient
+    of the Sobolev loss, update) at batch 4096 and the inference pass the surrogate evaluation runs
+    (value, input gradient and input Hessian) over a c5-sized set of points, each timed with CUDA
+    events on the launching stream over --steps repetitions after --warmup.  The 128 x 128 layer
+    products run on tcgen05; `gemm_tflops` divides their flops by the whole call's time (a lower
+    bound of the products' own rate)."""
+    import torch
+
+    import synth
+    from paper_1908_08292_gb300 import surrogate as su
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    B, n_inf = 4096, args.mlp_points
+    m = su.MLP(max(B, n_inf))
+    m.set_params(su.init_params(7))
+    x = torch.tensor(synth.random_field(81, n_inf, 6, 0.9), dtype=torch.float32, device=dev)
+    ty = torch.tensor(synth.random_field(82, 1, B, 1.0)[0], dtype=torch.float32, device=dev)
+    tg = torch.tensor(synth.random_field(83, B, 6, 1.0), dtype=torch.float32, device=dev)
+    y = torch.zeros(n_inf, dtype=torch.float32, device=dev)
+    g = torch.zeros(n_inf, 6, dtype=torch.float32, device=dev)
+    H = torch.zeros(n_inf, 6, 6, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def train_step():
+        m.loss_grad(x[:B], ty, tg, 1.0 / B, 1.0 / B, loss)
+        m.adamw(1e-4)
+
+    def infer():
+        m.eval(x, y, g, H)
+
+    def timed(fn, reps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = m.launches()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps, (m.launches() - l0) // reps
+
+    t_train, l_train = timed(train_step, args.steps)
+    t_inf, l_inf = timed(infer, args.steps)
+    m.check()
+    sq = 2.0 * 128 * 128
+    f_train = 18 * B * sq       # 128 x 128 products per training step
+    f_inf = (6 + 36) * n_inf * sq  # forward + backward (B rows) and 6 tangent directions (6B rows)
+    print(json.dumps({
+        "metric": "surrogate network: AdamW training steps/s (batch 4096) and inference points/s",
+        "value": 1.0 / t_train, "unit": "training steps/s", "workload": "mlp", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "bf16 operands, f32 accumulation",
+        "config": {"workload": f"MLP 6-4x128 SiLU-1, training batch {B}, inference {n_inf} points with "
+                               f"input gradient and Hessian", "steps": args.steps},
+        "train_ms": t_train * 1e3, "train_launches": int(l_train),
+        "train_gemm_tflops_lower_bound": f_train / t_train / 1e12,
+        "inference_points_per_s": n_inf / t_inf, "inference_ms": t_inf * 1e3, "inference_launches": int(l_inf),
+        "inference_gemm_tflops_lower_bound": f_inf / t_inf / 1e12,
     }))
 
 
@@ -1132,7 +1235,7 @@ def main():
                          "of --step-index from the zero state (short runs for profiling)")
     ap.add_argument("--precond", default="mg", choices=["mg", "jacobi"],
                     help="RVE PCG preconditioner: multigrid V-cycle (default; 2D) or block-Jacobi")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "schemes", "hconv"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "schemes", "hconv", "mlp"],
                     help="c2: 2D 4096 RVEs of 32x32 (default, the headline); c3: 3D 4096 uneven Hex8 RVEs; "
                          "c4: surrogate training; c5: surrogate+fallback vs plain macro iteration; "
                          "schemes: nested vs alternating load paths; hconv: micro mesh convergence and the KUBC "
@@ -1143,8 +1246,11 @@ def main():
     ap.add_argument("--c4-hessian-origin", type=int, default=1,
                     help="subtract the network's value, gradient and Hessian at E = 0 (1) or value and gradient (0)")
     ap.add_argument("--c4-save", default=None, help="write the trained surrogate to this file")
+    ap.add_argument("--c4-poly", type=int, default=6,
+                    help="maximum degree (3-6) of the polynomial part fitted before the network; 0: none")
     ap.add_argument("--c4-load", default=None, help="c5: use the surrogate in this file instead of training one")
     ap.add_argument("--c5-radius", type=float, default=0.3)
+    ap.add_argument("--mlp-points", type=int, default=32768, help="mlp: inference points per call")
     ap.add_argument("--c5-step", type=int, default=10)
     ap.add_argument("--c5-audit-stride", type=int, default=64)
     args = ap.parse_args()
@@ -1159,6 +1265,8 @@ def main():
         run_schemes(args)
     elif args.workload == "hconv":
         run_hconv(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     elif args.workload == "c5":
         _SIZE["macro"] = args.macro if args.macro is not None else 8
         args.macro = _SIZE["macro"]

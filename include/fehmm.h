@@ -296,7 +296,8 @@ int fehmm_macro_csr(fehmm_ctx* ctx, const int32_t** rowptr, const int32_t** col,
 /*
  * Energy surrogate (the learned part of the workload; the paper has no counterpart).
  * An MLP y(x), x in R^6 -> 4 x 128 SiLU -> 1, with BF16 weights and activations and FP32
- * accumulation on tensor cores.  Parameters are packed FP32 (fehmm_mlp_num_params floats):
+ * accumulation on tensor cores (the 128 x 128 layer products on tcgen05 with the accumulator in
+ * tensor memory, the 8-wide input-layer products on mma.sync).  Parameters are packed FP32 (fehmm_mlp_num_params floats):
  * W1 [128][8] (input columns 6, 7 unused), b1 [128], W2, W3, W4 [128][128] row-major
  * ([out][in]), b2..b4 [128], w5 [128], b5 [1], padding [3].  The context holds FP32 master
  * weights, BF16 copies, AdamW moments and a workspace for up to max_batch samples.
@@ -320,10 +321,15 @@ int fehmm_mlp_loss_grad(fehmm_mlp* mlp, const float* x, const float* ty, const f
 int fehmm_mlp_adamw(fehmm_mlp* mlp, float lr, float beta1, float beta2, float eps, float weight_decay,
                     void* stream);
 long long fehmm_mlp_launch_count(const fehmm_mlp* mlp);
+/* Synchronises the device and reports in *flag whether a tensor-core product of this MLP gave up
+ * waiting for its MMAs since the last check (1: its outputs are invalid; the flag is cleared). */
+int fehmm_mlp_check(fehmm_mlp* mlp, int* flag);
 /* Device view of the gradient that fehmm_mlp_loss_grad wrote and fehmm_mlp_adamw reads (FP32,
  * packed like the parameters; owned by the MLP).  Data-parallel training over ranks sums it over
  * the ranks between the two calls (each rank's loss weighted by 1/(global batch)). */
 int fehmm_mlp_grad_buffer(fehmm_mlp* mlp, float** dev_ptr, int* n_params);
+
+#define FEHMM_POLY_TERMS 896 /* monomials of degree 3 to 6 in 6 variables */
 
 typedef struct {
   double lam0, mu0;  /* Lame constants of the neo-Hookean base energy */
@@ -334,6 +340,11 @@ typedef struct {
   double y0, g0[6], H0[36]; /* network value, gradient and Hessian at x = 0, subtracted so that the
                         learned correction y(x) - y0 - g0.x - 1/2 x.H0.x vanishes to third order at
                         E = 0, where the base energy is exact to second order (zeros: no shift) */
+  double poly[FEHMM_POLY_TERMS]; /* fitted polynomial part of the correction, in network units:
+                        y_poly(x) = sum_a poly[a] x_{i1} x_{i2} ... x_{id} over the monomials of
+                        degree d = 3, 4, 5, 6 in the 6 features, each degree's index tuples
+                        i1 <= i2 <= ... <= id in lexicographic order (56 + 126 + 252 + 462 terms);
+                        W = W_base + sg (y_poly(x) + shifted network); zeros: no polynomial */
 } fehmm_surrogate_params;
 
 /*
@@ -366,6 +377,20 @@ int fehmm_surrogate_load(fehmm_mlp* mlp, fehmm_surrogate_params* sp, const char*
  * targets tg [n][6] (device floats) of the Sobolev loss of fehmm_mlp_loss_grad. */
 int fehmm_surrogate_targets(const fehmm_surrogate_params* sp, const double* F, const double* P, const double* W,
                             int n, float* x, float* ty, float* tg, void* stream);
+
+/* Polynomial part of the learned correction, fitted before the network (set-up; the paper has no
+ * counterpart).  Weighted linear least squares over the first min(n, 65536) samples of the
+ * training targets (device x [n][6], ty [n], tg [n][6] from fehmm_surrogate_targets): minimise
+ * sum_b [ (y_poly(x_b) - ty_b)^2 / <ty^2> + |grad y_poly(x_b) - tg_b|^2 / <|tg|^2> ] over the
+ * coefficients of the monomials of degree 3 to max_degree (3..6; the Sobolev loss of the network,
+ * normalised the same way), normal equations accumulated in FP64 on the device and solved by
+ * Cholesky on the host with a 1e-12 relative ridge.  Writes sp->poly (zero above max_degree) and
+ * replaces ty, tg of all n samples by their remainders (ty - y_poly, tg - grad y_poly), which the
+ * network then learns.  The polynomial has no terms below degree 3, so the third-order origin
+ * condition of the correction still holds.  FEHMM_ERR_ARG on bad arguments or a normal matrix
+ * that is not positive definite. */
+int fehmm_surrogate_fit_poly(fehmm_surrogate_params* sp, const float* x, float* ty, float* tg, int n,
+                             int max_degree, void* stream);
 
 /*
  * Autotuner of the solver settings (project-written; the paper has no counterpart).  Times the

@@ -89,6 +89,7 @@ _SIGS = {
     "fehmm_mlp_loss_grad": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, ctypes.c_float, _P, _P]),
     "fehmm_mlp_adamw": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
     "fehmm_mlp_launch_count": (ctypes.c_longlong, [_P]),
+    "fehmm_mlp_check": (_I, [_P, ctypes.POINTER(_I)]),
     "fehmm_mlp_grad_buffer": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I)]),
     "fehmm_surrogate_save": (_I, [_P, _P, ctypes.c_char_p]),
     "fehmm_surrogate_base_law": (_I, [_P, _P]),
@@ -96,6 +97,7 @@ _SIGS = {
     "fehmm_surrogate_eval": (_I, [_P, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
     "fehmm_surrogate_work_floats": (ctypes.c_size_t, [_I]),
     "fehmm_surrogate_targets": (_I, [_P, _P, _P, _P, _I, _P, _P, _P, _P]),
+    "fehmm_surrogate_fit_poly": (_I, [_P, _P, _P, _P, _I, _I, _P]),
     "fehmm_rve2d_solve_fp64_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options), _P]),
 }
 

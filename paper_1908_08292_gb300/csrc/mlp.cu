@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "fehmm.h"
+#include "tc_gemm.cuh"
 
 namespace fehmm {
 namespace {
@@ -402,6 +403,7 @@ struct fehmm_mlp {
   float* TD = nullptr;
   float* HK = nullptr;   // [6 B][8]
   int step = 0;
+  int* err = nullptr;     // set by a tensor-core GEMM whose mbarrier wait ran out
   std::vector<void*> allocs;
   long long launches = 0;
 };
@@ -426,8 +428,57 @@ int blocks_for(size_t n) {
   return (int)(b ? b : 1);
 }
 
+template <bool AM, bool BNM, int BN>
+cudaError_t launch_tc_bn(const tc::Args& a, dim3 grid, cudaStream_t s) {
+  using C = tc::Cfg<BN>;
+  // per launch: the attribute belongs to the current device
+  const cudaError_t e =
+      cudaFuncSetAttribute(tc::gemm_tc_kernel<AM, BNM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  tc::gemm_tc_kernel<AM, BNM, BN><<<grid, 128, C::kSmemBytes, s>>>(a);
+  return cudaSuccess;
+}
+
+template <bool AM, bool BNM>
+cudaError_t launch_tc(const tc::Args& a, int bn, dim3 grid, cudaStream_t s) {
+  if (bn == 32) return launch_tc_bn<AM, BNM, 32>(a, grid, s);
+  if (bn == 64) return launch_tc_bn<AM, BNM, 64>(a, grid, s);
+  return launch_tc_bn<AM, BNM, 128>(a, grid, s);
+}
+
+// Products with 64 < N <= 128 and K >= 64 (every 128 x 128 layer product, forward, backward and
+// weight gradient) run on tcgen05, 128-row tiles of C split into column tiles of 32 or 64 when
+// there are too few row tiles to fill the GPU; the narrow ones (the 6-wide input layer, N or K =
+// 8) on the mma.sync kernel.
 cudaError_t gemm(fehmm_mlp* mm, bool am, bool bnm, int M, int N, int K, const bf16* A, int lda, const bf16* B,
                  int ldb, float* C, int ldc, const float* bias, bool atomic, cudaStream_t s) {
+  if (N > 64 && N <= tc::kBNMax && K >= tc::kBK) {
+    tc::Args a{M, N, K, A, lda, B, ldb, C, ldc, bias, atomic ? 1 : 0, K, mm->err};
+    const int tiles = (M + tc::kBM - 1) / tc::kBM;
+    int splits = 1, bn = tc::kBNMax;
+    if (atomic) {  // split the batch reduction: chunks of >= 256, at most one CTA per SM in all
+      splits = (K + 255) / 256;
+      if (splits * tiles > 148) splits = 148 / tiles;
+      if (splits < 1) splits = 1;
+      a.k_split = ((K + splits - 1) / splits + tc::kBK - 1) / tc::kBK * tc::kBK;
+      splits = (K + a.k_split - 1) / a.k_split;
+    } else {
+      a.k_split = (K + tc::kBK - 1) / tc::kBK * tc::kBK;
+      bn = tiles >= 112 ? 128 : (tiles >= 56 ? 64 : 32);  // about 112+ CTAs on the 152 SMs
+    }
+    const dim3 grid(tiles, (N + bn - 1) / bn, splits);
+    cudaError_t e;
+    if (!am && !bnm)
+      e = launch_tc<false, false>(a, bn, grid, s);
+    else if (am && bnm)
+      e = launch_tc<true, true>(a, bn, grid, s);
+    else if (am)
+      e = launch_tc<true, false>(a, bn, grid, s);
+    else
+      e = launch_tc<false, true>(a, bn, grid, s);
+    mm->launches += 1;
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   GemmArgs g{M, N, K, A, lda, B, ldb, C, ldc, bias, atomic ? 1 : 0, K};
   int splits = 1;
   if (atomic) {  // split the batch reduction across blocks
@@ -525,12 +576,14 @@ int fehmm_mlp_create(fehmm_mlp** out, int max_batch) {
   for (int l = 1; l <= 4; ++l) rc |= alloc(m, m->ZD[l], 6 * BW);
   rc |= alloc(m, m->AD, 6 * BW);
   rc |= alloc(m, m->HK, 6 * B * NINP);
+  rc |= alloc(m, m->err, 1);
   if (rc != FEHMM_OK) {
     for (void* p : m->allocs) cudaFree(p);
     delete m;
     return FEHMM_ERR_OOM;
   }
   cudaMemset(m->P, 0, sizeof(float) * N_PARAMS);
+  cudaMemset(m->err, 0, sizeof(int));
   cudaMemset(m->m, 0, sizeof(float) * N_PARAMS);
   cudaMemset(m->v, 0, sizeof(float) * N_PARAMS);
   *out = m;
@@ -648,6 +701,14 @@ int fehmm_mlp_adamw(fehmm_mlp* m, float lr, float beta1, float beta2, float eps,
 
 long long fehmm_mlp_launch_count(const fehmm_mlp* m) { return m ? m->launches : -1; }
 
+int fehmm_mlp_check(fehmm_mlp* m, int* flag) {
+  if (!m || !flag) return FEHMM_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FEHMM_ERR_CUDA;
+  if (cudaMemcpy(flag, m->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FEHMM_ERR_CUDA;
+  if (*flag != 0 && cudaMemset(m->err, 0, sizeof(int)) != cudaSuccess) return FEHMM_ERR_CUDA;
+  return FEHMM_OK;
+}
+
 int fehmm_mlp_grad_buffer(fehmm_mlp* m, float** dev_ptr, int* n) {
   if (!m || !dev_ptr) return FEHMM_ERR_ARG;
   *dev_ptr = m->G;
@@ -660,7 +721,7 @@ int fehmm_mlp_grad_buffer(fehmm_mlp* m, float** dev_ptr, int* n) {
 // the struct is written, so a load reproduces the evaluation exactly).
 namespace {
 constexpr char kMagic[8] = {'F', 'E', 'H', 'M', 'M', 'S', 'U', 'R'};
-constexpr int32_t kFormat = 1;
+constexpr int32_t kFormat = 2;  // 2: with the polynomial part
 constexpr size_t kSpDoubles = sizeof(fehmm_surrogate_params) / sizeof(double);
 static_assert(sizeof(fehmm_surrogate_params) == kSpDoubles * sizeof(double), "surrogate params are all doubles");
 }  // namespace

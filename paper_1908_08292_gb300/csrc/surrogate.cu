@@ -12,9 +12,14 @@
 // closed forms for S and CC) with effective Lame constants (lam0, mu0); the network learns the
 // remainder.  Mandel order (11, 22, 33, 23, 13, 12) with sqrt(2) on the shear entries, so that
 // S_IJ = (sg/sx) g_p / w_p and CC_IJKL = (sg/sx^2) H_pq / (w_p w_q), w = 1 or sqrt(2).
+// The correction y is the sum of a fitted polynomial of degree 3 to 5 in x (weighted linear
+// least squares on the training targets, fehmm_surrogate_fit_poly) and the network, which learns
+// what the polynomial leaves; both vanish to third order at x = 0.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <vector>
 
 #include "fehmm.h"
 
@@ -49,6 +54,102 @@ __device__ __forceinline__ int mandel_index(int I, int J) {
   if (I == J) return I;
   const int a = I < J ? I : J, b = I < J ? J : I;
   return (a == 1 && b == 2) ? 3 : (a == 0 && b == 2) ? 4 : 5;
+}
+
+// ------------------------------------------------------------------ polynomial part
+constexpr int kPolyTerms = FEHMM_POLY_TERMS;
+constexpr int kPolyMaxDeg = 6;
+
+// Index tuples of the monomials: degree 3, 4, 5, 6, each in lexicographic order of the
+// nondecreasing tuples (i1 <= ... <= id); unused positions hold 6 (the factor 1).
+struct MonoTable {
+  unsigned char idx[kPolyTerms][kPolyMaxDeg];
+  unsigned char deg[kPolyTerms];
+  int count;
+};
+
+constexpr MonoTable make_monomials() {
+  MonoTable t{};
+  int c = 0;
+  for (int d = 3; d <= kPolyMaxDeg; ++d) {
+    int a[kPolyMaxDeg] = {0, 0, 0, 0, 0, 0};
+    for (;;) {
+      if (c < kPolyTerms) {
+        for (int k = 0; k < kPolyMaxDeg; ++k) t.idx[c][k] = (unsigned char)(k < d ? a[k] : 6);
+        t.deg[c] = (unsigned char)d;
+      }
+      ++c;
+      int k = d - 1;
+      while (k >= 0 && a[k] == 5) --k;
+      if (k < 0) break;
+      ++a[k];
+      for (int m = k + 1; m < d; ++m) a[m] = a[k];
+    }
+  }
+  t.count = c;
+  return t;
+}
+
+constexpr MonoTable kMonoHost = make_monomials();
+static_assert(kMonoHost.count == kPolyTerms, "56 + 126 + 252 + 462 monomials of degree 3..6 in 6 variables");
+
+// terms of degree <= d (the coefficients are ordered by degree)
+__host__ __device__ constexpr int poly_terms_upto(int d) {
+  return d <= 2 ? 0 : d == 3 ? 56 : d == 4 ? 182 : d == 5 ? 434 : 896;
+}
+__constant__ MonoTable kMono = make_monomials();
+
+// Factors of monomial c at x (padded with ones) and the products of all factors but one.
+__device__ __forceinline__ void mono_factors(int c, const double (&x7)[7], double (&v)[kPolyMaxDeg],
+                                             int (&id)[kPolyMaxDeg]) {
+#pragma unroll
+  for (int k = 0; k < kPolyMaxDeg; ++k) {
+    id[k] = kMono.idx[c][k];
+    v[k] = x7[id[k]];
+  }
+}
+
+// y_poly, its gradient and (H != null) Hessian at x (FP64), coefficients coef[kPolyTerms].
+__device__ void poly_eval(const double* coef, const double (&x)[6], double& y, double (&g)[6], double* H) {
+  double x7[7];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) x7[k] = x[k];
+  x7[6] = 1.0;
+  y = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) g[k] = 0.0;
+  if (H)
+    for (int k = 0; k < 36; ++k) H[k] = 0.0;
+  for (int c = 0; c < kPolyTerms; ++c) {
+    const double a = coef[c];
+    if (a == 0.0) continue;
+    double v[kPolyMaxDeg];
+    int id[kPolyMaxDeg];
+    mono_factors(c, x7, v, id);
+    const int d = kMono.deg[c];
+    y += a * (v[0] * v[1] * v[2] * v[3] * v[4] * v[5]);
+#pragma unroll
+    for (int i = 0; i < kPolyMaxDeg; ++i) {
+      if (i >= d) break;
+      double pe = a;
+#pragma unroll
+      for (int k = 0; k < kPolyMaxDeg; ++k)
+        if (k != i) pe *= v[k];
+      g[id[i]] += pe;
+      if (H) {
+#pragma unroll
+        for (int j = i + 1; j < kPolyMaxDeg; ++j) {
+          if (j >= d) break;
+          double pij = a;
+#pragma unroll
+          for (int k = 0; k < kPolyMaxDeg; ++k)
+            if (k != i && k != j) pij *= v[k];
+          H[6 * id[i] + id[j]] += pij;
+          H[6 * id[j] + id[i]] += pij;
+        }
+      }
+    }
+  }
 }
 
 // eigenvalues of a symmetric 3x3 matrix (trigonometric closed form)
@@ -98,7 +199,8 @@ __global__ void features_kernel(const double* F, int n, double sx, double radius
 }
 
 __global__ void combine_kernel(const double* F, int n, double lam0, double mu0, double sx, double sg, const BaseAniso ba,
-                               const float* y, const float* g, const float* H, double* P, double* A, double* Wout) {
+                               const double* coef, const float* y, const float* g, const float* H, double* P, double* A,
+                               double* Wout) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const double* f = F + (size_t)q * 9;
@@ -121,11 +223,13 @@ __global__ void combine_kernel(const double* F, int n, double lam0, double mu0, 
     const int I = kMandelI[p], J = kMandelJ[p];
     xs[p] = (I == J ? 1.0 : sq2) * 0.5 * (C[3 * I + J] - (I == J ? 1.0 : 0.0)) / sx;
   }
-  ys = (double)y[q] - ba.y0;
+  double yp, gp[6], Hp[36];
+  poly_eval(coef, xs, yp, gp, A ? Hp : nullptr);
+  ys = (double)y[q] - ba.y0 + yp;
   for (int p = 0; p < 6; ++p) {
     double hx = 0.0;
     for (int r = 0; r < 6; ++r) hx += ba.H0[6 * p + r] * xs[r];
-    gs[p] = (double)g[(size_t)q * 6 + p] - ba.g0[p] - hx;
+    gs[p] = (double)g[(size_t)q * 6 + p] - ba.g0[p] - hx + gp[p];
     ys -= (ba.g0[p] + 0.5 * hx) * xs[p];
   }
   for (int I = 0; I < 3; ++I)
@@ -154,7 +258,7 @@ __global__ void combine_kernel(const double* F, int n, double lam0, double mu0, 
                                      gam * Ci[3 * I + Jj] * Ci[3 * K + L];
               const int pp = mandel_index(I, Jj), qq = mandel_index(K, L);
               const double wp = (I == Jj) ? 1.0 : sq2, wq = (K == L) ? 1.0 : sq2;
-              const double hn = (double)Hq[pp * 6 + qq] - ba.H0[6 * pp + qq];
+              const double hn = (double)Hq[pp * 6 + qq] - ba.H0[6 * pp + qq] + Hp[6 * pp + qq];
               const double cc = cc_base + (sg / (sx * sx) * hn + ba.Ca[6 * pp + qq]) / (wp * wq);
               acc += f[3 * i + I] * f[3 * k + K] * cc;
             }
@@ -232,6 +336,155 @@ __global__ void compact_kernel(const int32_t* mask, int n, int value, int stride
   if (threadIdx.x == 0) *count = base;
 }
 
+
+// ------------------------------------------------------------------ polynomial fit
+constexpr int kFitTile = 32;
+constexpr int kFitChunk = 12;              // samples per shared-memory chunk (7 rows each)
+constexpr int kFitRows = 7 * kFitChunk;
+constexpr int kFitMaxSamples = 65536;
+
+// sums of ty^2 and |tg|^2 over the fit samples (the loss normalisation)
+__global__ void fit_norms_kernel(const float* ty, const float* tg, int n, double* out) {
+  double a = 0.0, b = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    a += (double)ty[q] * ty[q];
+    for (int k = 0; k < 6; ++k) b += (double)tg[(size_t)q * 6 + k] * tg[(size_t)q * 6 + k];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], a);
+    atomicAdd(&out[1], b);
+  }
+}
+
+// The 7 rows (value, 6 partial derivatives) of column col for a sample at features x, each
+// scaled by the square root of its weight; the target column holds ty, tg.
+__device__ __forceinline__ void fit_column(int col, int nt, const double (&x7)[7], float tyv, const float* tgv,
+                                           double ry, double rg, double (&r)[7]) {
+  if (col > nt) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) r[k] = 0.0;
+    return;
+  }
+  if (col == nt) {
+    r[0] = ry * tyv;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r[1 + k] = rg * tgv[k];
+    return;
+  }
+  double v[kPolyMaxDeg];
+  int id[kPolyMaxDeg];
+  mono_factors(col, x7, v, id);
+  const int d = kMono.deg[col];
+  r[0] = ry * (v[0] * v[1] * v[2] * v[3] * v[4] * v[5]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r[1 + k] = 0.0;
+#pragma unroll
+  for (int i = 0; i < kPolyMaxDeg; ++i) {
+    if (i >= d) break;
+    double pe = rg;
+#pragma unroll
+    for (int k = 0; k < kPolyMaxDeg; ++k)
+      if (k != i) pe *= v[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (id[i] == k) r[1 + k] += pe;
+  }
+}
+
+// G[i][j] += sum over rows of phi_i phi_j (nt monomial columns and the target column nt, G is
+// (nt + 1)^2) for the column tiles (ti <= tj) of blockIdx.x, over the sample slice blockIdx.y.
+// FP64 throughout; block partials added to G atomically.
+__global__ void __launch_bounds__(256) fit_normal_kernel(const float* x, const float* ty, const float* tg, int n,
+                                                         int nt, const double* norms, double* G) {
+  __shared__ double Pi[kFitRows][kFitTile + 1], Pj[kFitRows][kFitTile + 1];
+  const int cols = nt + 1, tiles = (cols + kFitTile - 1) / kFitTile;
+  int ti = 0, rem = blockIdx.x;
+  while (rem >= tiles - ti) {
+    rem -= tiles - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
+  const double ry = sqrt((double)n / fmax(norms[0], 1e-300)), rg = sqrt((double)n / fmax(norms[1], 1e-300));
+  const int per = (n + gridDim.y - 1) / gridDim.y;
+  const int s_begin = blockIdx.y * per, s_end = min(n, s_begin + per);
+  const int t = threadIdx.x, cc = t & 31, r0 = t >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int s0 = s_begin; s0 < s_end; s0 += kFitChunk) {
+    for (int item = t; item < 2 * kFitChunk * kFitTile; item += blockDim.x) {
+      const int which = item / (kFitChunk * kFitTile), rest = item % (kFitChunk * kFitTile);
+      const int ls = rest / kFitTile, col = rest % kFitTile, sidx = s0 + ls;
+      double r[7];
+      if (sidx < s_end) {
+        double x7[7];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x7[k] = (double)x[(size_t)sidx * 6 + k];
+        x7[6] = 1.0;
+        fit_column((which ? tj : ti) * kFitTile + col, nt, x7, ty[sidx], tg + (size_t)sidx * 6, ry, rg, r);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) r[k] = 0.0;
+      }
+      double(*Pd)[kFitTile + 1] = which ? Pj : Pi;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) Pd[7 * ls + k][col] = r[k];
+    }
+    __syncthreads();
+    for (int row = 0; row < kFitRows; ++row) {
+      const double bj = Pj[row][cc];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[m] = fma(Pi[row][r0 + 8 * m], bj, acc[m]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int gi = ti * kFitTile + r0 + 8 * m, gj = tj * kFitTile + cc;
+    if (gi < cols && gj < cols) atomicAdd(&G[(size_t)gi * cols + gj], acc[m]);
+  }
+}
+
+// ty -= y_poly(x), tg -= grad y_poly(x) for every sample
+__global__ void fit_subtract_kernel(const double* coef, const float* x, int n, float* ty, float* tg) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  double xs[6], y, g[6];
+  for (int k = 0; k < 6; ++k) xs[k] = (double)x[(size_t)q * 6 + k];
+  poly_eval(coef, xs, y, g, nullptr);
+  ty[q] = (float)((double)ty[q] - y);
+  for (int k = 0; k < 6; ++k) tg[(size_t)q * 6 + k] = (float)((double)tg[(size_t)q * 6 + k] - g[k]);
+}
+
+// Cholesky solve of the symmetric positive definite system A c = b (host, in place on a copy)
+bool cholesky_solve(std::vector<double>& A, int N, std::vector<double>& b) {
+  for (int j = 0; j < N; ++j) {
+    double d = A[(size_t)j * N + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)j * N + k] * A[(size_t)j * N + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = sqrt(d);
+    A[(size_t)j * N + j] = ljj;
+    for (int i = j + 1; i < N; ++i) {
+      double v = A[(size_t)i * N + j];
+      for (int k = 0; k < j; ++k) v -= A[(size_t)i * N + k] * A[(size_t)j * N + k];
+      A[(size_t)i * N + j] = v / ljj;
+    }
+  }
+  for (int i = 0; i < N; ++i) {  // L z = b
+    double v = b[i];
+    for (int k = 0; k < i; ++k) v -= A[(size_t)i * N + k] * b[k];
+    b[i] = v / A[(size_t)i * N + i];
+  }
+  for (int i = N - 1; i >= 0; --i) {  // L^T c = z
+    double v = b[i];
+    for (int k = i + 1; k < N; ++k) v -= A[(size_t)k * N + i] * b[k];
+    b[i] = v / A[(size_t)i * N + i];
+  }
+  return true;
+}
+
 }  // namespace
 }  // namespace fehmm
 
@@ -244,11 +497,15 @@ extern "C" int fehmm_surrogate_eval(fehmm_mlp* mlp, const fehmm_surrogate_params
   if (!mlp || !sp || !F || !P || !inside || !work || n <= 0) return FEHMM_ERR_ARG;
   if (!(sp->sx > 0) || !(sp->sg > 0) || !(sp->radius >= 0)) return FEHMM_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  float* x = work;                 // [n][6]
-  float* y = x + (size_t)n * 6;    // [n]
+  double* coef = reinterpret_cast<double*>(work);  // [kPolyTerms], then the float arrays
+  float* x = work + 2 * kPolyTerms;                 // [n][6]
+  float* y = x + (size_t)n * 6;                     // [n]
   float* g = y + n;                // [n][6]
   float* H = g + (size_t)n * 6;    // [n][36]
   const int blocks = (n + 127) / 128;
+  if (reinterpret_cast<uintptr_t>(work) % 8 != 0) return FEHMM_ERR_ARG;
+  if (cudaMemcpyAsync(coef, sp->poly, sizeof(double) * kPolyTerms, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FEHMM_ERR_CUDA;
   features_kernel<<<blocks, 128, 0, s>>>(F, n, sp->sx, sp->radius, x, inside);
   int rc = fehmm_mlp_eval(mlp, x, n, y, g, A ? H : nullptr, stream);
   if (rc != FEHMM_OK) return rc;
@@ -259,11 +516,11 @@ extern "C" int fehmm_surrogate_eval(fehmm_mlp* mlp, const fehmm_surrogate_params
   }
   for (int k = 0; k < 6; ++k) ba.g0[k] = sp->g0[k];
   ba.y0 = sp->y0;
-  combine_kernel<<<blocks, 128, 0, s>>>(F, n, sp->lam0, sp->mu0, sp->sx, sp->sg, ba, y, g, H, P, A, W);
+  combine_kernel<<<blocks, 128, 0, s>>>(F, n, sp->lam0, sp->mu0, sp->sx, sp->sg, ba, coef, y, g, H, P, A, W);
   return cudaGetLastError() == cudaSuccess ? FEHMM_OK : FEHMM_ERR_CUDA;
 }
 
-extern "C" size_t fehmm_surrogate_work_floats(int n) { return (size_t)n * (6 + 1 + 6 + 36); }
+extern "C" size_t fehmm_surrogate_work_floats(int n) { return 2 * (size_t)kPolyTerms + (size_t)n * (6 + 1 + 6 + 36); }
 
 extern "C" int fehmm_select(const int32_t* mask, int n, int value, int stride, int32_t* list, int32_t* count,
                             void* stream) {
@@ -314,4 +571,62 @@ extern "C" int fehmm_surrogate_base_law(const double* A0, fehmm_surrogate_params
   sp->lam0 = lam;
   sp->mu0 = mu;
   return FEHMM_OK;
+}
+
+extern "C" int fehmm_surrogate_fit_poly(fehmm_surrogate_params* sp, const float* x, float* ty, float* tg, int n,
+                                        int max_degree, void* stream) {
+  if (!sp || !x || !ty || !tg || n <= 0 || max_degree < 3 || max_degree > kPolyMaxDeg) return FEHMM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nf = n < kFitMaxSamples ? n : kFitMaxSamples;
+  const int N = poly_terms_upto(max_degree), cols = N + 1, tiles = (cols + kFitTile - 1) / kFitTile;
+  double* d = nullptr;  // norms [2], G [cols^2], coefficients [kPolyTerms]
+  const size_t nG = (size_t)cols * cols;
+  if (cudaMalloc(&d, sizeof(double) * (2 + nG + kPolyTerms)) != cudaSuccess) {
+    cudaGetLastError();
+    return FEHMM_ERR_OOM;
+  }
+  double* norms = d;
+  double* G = d + 2;
+  double* coef = G + nG;
+  int rc = FEHMM_OK;
+  std::vector<double> Gh(nG);
+  if (cudaMemsetAsync(d, 0, sizeof(double) * (2 + nG), s) != cudaSuccess) rc = FEHMM_ERR_CUDA;
+  if (rc == FEHMM_OK) {
+    fit_norms_kernel<<<64, 256, 0, s>>>(ty, tg, nf, norms);
+    const int pairs = tiles * (tiles + 1) / 2;
+    fit_normal_kernel<<<dim3(pairs, 8), 256, 0, s>>>(x, ty, tg, nf, N, norms, G);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(Gh.data(), G, sizeof(double) * nG, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = FEHMM_ERR_CUDA;
+  }
+  std::vector<double> c(kPolyTerms, 0.0);
+  if (rc == FEHMM_OK) {
+    // entry (i, j) was accumulated where tile(i) <= tile(j): take it from there
+    std::vector<double> A((size_t)N * N), b(N);
+    double tr = 0.0;
+    for (int i = 0; i < N; ++i) {
+      for (int j = 0; j < N; ++j) {
+        const bool up = (i / kFitTile) <= (j / kFitTile);
+        A[(size_t)i * N + j] = up ? Gh[(size_t)i * cols + j] : Gh[(size_t)j * cols + i];
+      }
+      b[i] = Gh[(size_t)i * cols + N];
+      tr += A[(size_t)i * N + i];
+    }
+    for (int i = 0; i < N; ++i) A[(size_t)i * N + i] += 1e-12 * tr / N;
+    if (!cholesky_solve(A, N, b)) rc = FEHMM_ERR_ARG;
+    for (int i = 0; i < N; ++i) c[i] = b[i];
+  }
+  if (rc == FEHMM_OK) {
+    if (cudaMemcpyAsync(coef, c.data(), sizeof(double) * kPolyTerms, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      rc = FEHMM_ERR_CUDA;
+    } else {
+      fit_subtract_kernel<<<(n + 127) / 128, 128, 0, s>>>(coef, x, n, ty, tg);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = FEHMM_ERR_CUDA;
+    }
+  }
+  cudaFree(d);
+  if (rc == FEHMM_OK)
+    for (int k = 0; k < kPolyTerms; ++k) sp->poly[k] = c[k];
+  return rc;
 }

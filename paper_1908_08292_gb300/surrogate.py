@@ -135,11 +135,27 @@ class MLP:
         _check(lib().fehmm_mlp_adamw(self._h, float(lr), float(beta1), float(beta2), float(eps),
                                      float(weight_decay), _stream(stream)), "mlp_adamw")
 
+    def launches(self):
+        """Kernels this MLP has launched so far."""
+        return int(lib().fehmm_mlp_launch_count(self._h))
+
+    def check(self):
+        """Synchronise; raise if a tensor-core product gave up waiting for its MMAs since the
+        last check (its outputs are then invalid)."""
+        flag = ctypes.c_int(0)
+        _check(lib().fehmm_mlp_check(self._h, ctypes.byref(flag)), "mlp_check")
+        if flag.value:
+            raise RuntimeError("fehmm: a tensor-core matrix product timed out waiting for its MMAs")
+
+
+POLY_TERMS = 896  # monomials of degree 3..6 in the 6 features (FEHMM_POLY_TERMS)
+
 
 class SurrogateParams(ctypes.Structure):
     _fields_ = [("lam0", ctypes.c_double), ("mu0", ctypes.c_double), ("sx", ctypes.c_double),
                 ("sg", ctypes.c_double), ("radius", ctypes.c_double), ("Ca", ctypes.c_double * 36),
-                ("y0", ctypes.c_double), ("g0", ctypes.c_double * 6), ("H0", ctypes.c_double * 36)]
+                ("y0", ctypes.c_double), ("g0", ctypes.c_double * 6), ("H0", ctypes.c_double * 36),
+                ("poly", ctypes.c_double * POLY_TERMS)]
 
     def set_Ca(self, M):
         M = np.asarray(M, dtype=np.float64).reshape(36)
@@ -184,6 +200,18 @@ def surrogate_eval(mlp: MLP, sp: SurrogateParams, F, P, A, W, inside, work, stre
                                       _dev(W, torch.float64, "W"), _dev(inside, torch.int32, "inside", n),
                                       _dev(work, torch.float32, "work", work_floats(n)), _stream(stream)),
            "surrogate_eval")
+
+
+def fit_poly(sp: SurrogateParams, x, ty, tg, max_degree=6, stream=None):
+    """Fit the polynomial part of the correction (monomials of degree 3..max_degree) to the
+    training targets (device x, ty, tg from surrogate_targets) by the library
+    (fehmm_surrogate_fit_poly): sets sp.poly and replaces ty, tg in place by what the polynomial
+    leaves for the network."""
+    import torch
+    n = x.shape[0]
+    _check(lib().fehmm_surrogate_fit_poly(ctypes.byref(sp), _dev(x, torch.float32, "x", 6 * n),
+                                          _dev(ty, torch.float32, "ty", n), _dev(tg, torch.float32, "tg", 6 * n), n,
+                                          int(max_degree), _stream(stream)), "surrogate_fit_poly")
 
 
 def work_floats(n: int) -> int:
@@ -313,6 +341,7 @@ def train(mlp, x, ty, tg, epochs, batch=4096, lr=2e-3, lr_end=2e-5, weight_decay
         hist.append(float(loss.item()))
         if log:
             log(f"epoch {ep} loss {hist[-1]:.3e}")
+    mlp.check()
     return hist
 
 

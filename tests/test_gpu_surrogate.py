@@ -62,6 +62,18 @@ def test_surrogate_accuracy_gain_and_speed():
     assert rms < 3e-3, rms
     assert t_sur < 0.05 * t_rve, (t_sur, t_rve)
 
+    # the polynomial part fitted to the same targets already takes most of the base law's error
+    spp = su.SurrogateParams(lam0, mu0, 0.35, 0.01 * (lam0 + 2 * mu0), 0.3)
+    spp.set_Ca(Ca)
+    typ, tgp = ty.clone(), tg.clone()
+    su.fit_poly(spp, x, typ, tgp)
+    su.surrogate_eval(zero, spp, F, Ps, As, None, ins, work)
+    torch.cuda.synchronize()
+    rms_p = np.sqrt((su.stress_errors(Ps.cpu().numpy(), Ph.cpu().numpy(), 1e-3) ** 2).mean())
+    assert rms_p < rms0 / 3, (rms_p, rms0)
+    # and what it leaves is smaller than what the network had to learn without it
+    assert float((tgp.double() ** 2).sum()) < float((tg.double() ** 2).sum()) / 9
+
 
 def test_fallback_replaces_points_outside_trust_region():
     """Points outside the trust region get exactly the full RVE solution; inside, the surrogate."""
