@@ -73,9 +73,13 @@ FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
 
 # DRAM bytes per RVE solve of the dominant kernel from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch / RVEs in that launch), with the profile summary it comes
-# from; scaled to a launch of the bench by the RVEs it solves.  Empty until the current kernel
-# has been captured.
-TRAFFIC_PER_LAUNCH = {}
+# from; scaled to a launch of the bench by the RVEs it solves.  Captured on smaller launches of
+# the same kernel build (1024 RVEs of c2, 64 of c3); the bytes per RVE are the state each solve
+# reads and writes plus scratch write-back, which grow with the RVEs of a launch.
+TRAFFIC_PER_LAUNCH = {
+    ("c2", "mg"): ((53123072 + 105645568) / 1024, "profiles/rve2d_kernel_mg_c2_macro16.md"),
+    ("c3", "mg"): ((1031852000 + 500233472) / 64, "profiles/rve3d_kernel_mg_c3_macro2.md"),
+}
 
 
 def workload_config(step_index):
@@ -841,7 +845,7 @@ def run_c4(args):
         torch.cuda.synchronize()
         t_fit = time.perf_counter() - t3
     mlp = su.MLP(4096)
-    mlp.set_params(su.init_params(7))
+    mlp.set_params(su.init_params(7, out_scale=args.c4_out_scale))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     hist = su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096)
@@ -908,7 +912,8 @@ def run_c4(args):
         "higher_is_better": True, "workload": "c4",
         "config": {"workload": f"fixed 12^3 two-inclusion RVE (ratio 10), {args.c4_samples} training U in "
                                f"|U-I|_F<=0.3, {args.c4_holdout} held-out, MLP 6-4x128 SiLU-1 BF16/FP32, AdamW "
-                               f"batch 4096, {args.c4_epochs} epochs, Sobolev loss (W and S), origin shift to "
+                               f"batch 4096, {args.c4_epochs} epochs, output layer initialised x{args.c4_out_scale}, "
+                               f"Sobolev loss (W and S), origin shift to "
                                f"{'third' if args.c4_hessian_origin else 'second'} order"
                                + (f", polynomial part of degree 3-{args.c4_poly} fitted first" if args.c4_poly else "")},
         "dropped_failed_solves": dropped + dropped_h, "base_law": {"lam0": lam0, "mu0": mu0},
@@ -950,7 +955,7 @@ def run_c5(args):
         x, ty, tg, _, _, _ = su.generate(gen, sp, synth.stretch_ball(1004, args.c4_samples, 0.3))
         if args.c4_poly:
             su.fit_poly(sp, x, ty, tg, max_degree=args.c4_poly)
-        mlp.set_params(su.init_params(7))
+        mlp.set_params(su.init_params(7, out_scale=args.c4_out_scale))
         su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096)
         sp.set_origin(mlp, hessian=args.c4_hessian_origin)
         gen.close()
@@ -1242,7 +1247,9 @@ def main():
                          "modelling error")
     ap.add_argument("--c4-samples", type=int, default=204800)
     ap.add_argument("--c4-holdout", type=int, default=10240)
-    ap.add_argument("--c4-epochs", type=int, default=600)
+    ap.add_argument("--c4-epochs", type=int, default=2400)
+    ap.add_argument("--c4-out-scale", type=float, default=0.0,
+                    help="scale of the network's initial output weights (0: zero output layer)")
     ap.add_argument("--c4-hessian-origin", type=int, default=1,
                     help="subtract the network's value, gradient and Hessian at E = 0 (1) or value and gradient (0)")
     ap.add_argument("--c4-save", default=None, help="write the trained surrogate to this file")

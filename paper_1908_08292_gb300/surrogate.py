@@ -61,8 +61,10 @@ def unpack(v) -> dict:
     return out
 
 
-def init_params(seed: int) -> dict:
-    """He-uniform weights from the SplitMix64 input generator, zero biases."""
+def init_params(seed: int, out_scale: float = 1.0) -> dict:
+    """He-uniform weights from the SplitMix64 input generator, zero biases; the output weights
+    scaled by out_scale (0: a zero output layer, so that training starts from y = 0, for targets
+    far smaller than the initial network's output, e.g. what a fitted polynomial leaves)."""
     import synth
     p = {}
     fan = [N_IN, WIDTH, WIDTH, WIDTH]
@@ -70,7 +72,7 @@ def init_params(seed: int) -> dict:
         b = math.sqrt(6.0 / fan[l])
         p[f"W{l + 1}"] = b * (2 * synth.uniform(seed, np.arange(WIDTH) + 1000 * l, fan[l]) - 1)
         p[f"b{l + 1}"] = np.zeros(WIDTH)
-    p["w5"] = math.sqrt(3.0 / WIDTH) * (2 * synth.uniform(seed, np.array([999999]), WIDTH)[0] - 1)
+    p["w5"] = out_scale * math.sqrt(3.0 / WIDTH) * (2 * synth.uniform(seed, np.array([999999]), WIDTH)[0] - 1)
     p["b5"] = np.zeros(1)
     return p
 
