@@ -368,6 +368,19 @@ def run_gpu(args):
         path.append({"step": k, "ms": e0.elapsed_time(e1), "rve_passes": rec["rve_passes"],
                      "macro_iters": rec["macro_iters"], "converged": rec["converged"]})
 
+    tuned, t_tune = None, 0.0
+    if args.autotune == "on" or (args.autotune == "auto" and wl == "c3"):
+        # the solver settings for the timed steps, timed on a sample of the points solving the
+        # last load step of the path: from the fluctuations committed before it, at the macro
+        # deformation it converged to (the snapshots do not depend on the settings)
+        ctx.macro_qp_F(drv.u, drv.F)
+        F_last = drv.F.clone()
+        drv.restore(snaps[max(steps_timed)])
+        t3 = time.perf_counter()
+        tuned = ctx.autotune(F_last, n_sample=0)
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - t3
+
     def restore(k):
         drv.restore(snaps[k])
         flush.zero_()
@@ -498,6 +511,7 @@ def run_gpu(args):
         "rve_preconditioner": ("multigrid V(1,1) with Galerkin coarse levels" if args.precond == "mg"
                                else "block-Jacobi"),
         "timed_steps_converged": all(r["converged"] for r in recs),
+        "autotuned": ({"choice": tuned, "seconds": t_tune} if tuned is not None else None),
         "per_load_step": per_step,
         "load_path": {"steps": len(path), "seconds": sum(x["ms"] for x in path) / 1e3,
                       "rve_solves": sum(x["rve_passes"] for x in path) * n_total,
@@ -848,7 +862,7 @@ def run_c4(args):
     mlp.set_params(su.init_params(7, out_scale=args.c4_out_scale))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    hist = su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096)
+    hist = su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096, lr=args.c4_lr, lr_end=args.c4_lr / 100)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     steps = args.c4_epochs * (x.shape[0] // 4096)
@@ -912,7 +926,8 @@ def run_c4(args):
         "higher_is_better": True, "workload": "c4",
         "config": {"workload": f"fixed 12^3 two-inclusion RVE (ratio 10), {args.c4_samples} training U in "
                                f"|U-I|_F<=0.3, {args.c4_holdout} held-out, MLP 6-4x128 SiLU-1 BF16/FP32, AdamW "
-                               f"batch 4096, {args.c4_epochs} epochs, output layer initialised x{args.c4_out_scale}, "
+                               f"batch 4096, {args.c4_epochs} epochs, lr {args.c4_lr:g} cosine to 1/100, output layer "
+                               f"initialised x{args.c4_out_scale}, "
                                f"Sobolev loss (W and S), origin shift to "
                                f"{'third' if args.c4_hessian_origin else 'second'} order"
                                + (f", polynomial part of degree 3-{args.c4_poly} fitted first" if args.c4_poly else "")},
@@ -956,7 +971,7 @@ def run_c5(args):
         if args.c4_poly:
             su.fit_poly(sp, x, ty, tg, max_degree=args.c4_poly)
         mlp.set_params(su.init_params(7, out_scale=args.c4_out_scale))
-        su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096)
+        su.train(mlp, x, ty, tg, args.c4_epochs, batch=4096, lr=args.c4_lr, lr_end=args.c4_lr / 100)
         sp.set_origin(mlp, hessian=args.c4_hessian_origin)
         gen.close()
     p = _u_ball_problem(args.macro)
@@ -1248,11 +1263,14 @@ def main():
     ap.add_argument("--c4-samples", type=int, default=204800)
     ap.add_argument("--c4-holdout", type=int, default=10240)
     ap.add_argument("--c4-epochs", type=int, default=2400)
+    ap.add_argument("--c4-lr", type=float, default=2e-3, help="peak AdamW learning rate (cosine decay to 1/100)")
     ap.add_argument("--c4-out-scale", type=float, default=0.0,
                     help="scale of the network's initial output weights (0: zero output layer)")
     ap.add_argument("--c4-hessian-origin", type=int, default=1,
                     help="subtract the network's value, gradient and Hessian at E = 0 (1) or value and gradient (0)")
     ap.add_argument("--c4-save", default=None, help="write the trained surrogate to this file")
+    ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
+                    help="path mode: autotune the solver settings before the timed steps (auto: c3 only)")
     ap.add_argument("--c4-poly", type=int, default=6,
                     help="maximum degree (3-6) of the polynomial part fitted before the network; 0: none")
     ap.add_argument("--c4-load", default=None, help="c5: use the surrogate in this file instead of training one")
