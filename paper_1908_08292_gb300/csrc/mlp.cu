@@ -20,6 +20,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -431,10 +432,18 @@ int blocks_for(size_t n) {
 template <bool AM, bool BNM, int BN>
 cudaError_t launch_tc_bn(const tc::Args& a, dim3 grid, cudaStream_t s) {
   using C = tc::Cfg<BN>;
-  // per launch: the attribute belongs to the current device
-  const cudaError_t e =
-      cudaFuncSetAttribute(tc::gemm_tc_kernel<AM, BNM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  // the shared-memory attribute belongs to a device: set once per device for this instantiation
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (!bit || !(done.load(std::memory_order_relaxed) & bit)) {
+    e = cudaFuncSetAttribute(tc::gemm_tc_kernel<AM, BNM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(bit, std::memory_order_relaxed);
+  }
   tc::gemm_tc_kernel<AM, BNM, BN><<<grid, 128, C::kSmemBytes, s>>>(a);
   return cudaSuccess;
 }
