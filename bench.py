@@ -163,10 +163,10 @@ def build_problem(step_index):
     """The workload and the macro deformation gradient of the affine first iterate of the step."""
     import synth
     if _SIZE["workload"] == "c3":
-        p = synth.config3(macro=_SIZE["macro"])
+        p = synth.uniaxial_3d_uneven(macro=_SIZE["macro"])
         F = np.diag([1.0 + 0.2 * step_index / N_STEPS_C3, 1.0, 1.0])
         return p, F
-    p = synth.config2(macro=_SIZE["macro"], rve=RVE_N, macro_y=_SIZE["macro"] * _SIZE["world"])
+    p = synth.biaxial_shear_2d(macro=_SIZE["macro"], rve=RVE_N, macro_y=_SIZE["macro"] * _SIZE["world"])
     lam = step_index / N_STEPS
     F = np.eye(2) + lam * (p.extra["F_end"] - np.eye(2))
     return p, F
@@ -722,7 +722,7 @@ def run_gpu_iteration(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed: FP64 residual/sums, FP32 tangent/PCG)",
-        "data": "synthetic (seeded generator, config-2 shapes)", "config": workload_config(args.step_index),
+        "data": "synthetic (seeded generator, the 2D 4096-RVE workload's shapes)", "config": workload_config(args.step_index),
         "micro_dof_newton_iter_per_s": dof_iter,
         "rve_preconditioner": ("multigrid V(1,1) with Galerkin coarse levels" if args.precond == "mg"
                                else "block-Jacobi"),
@@ -808,13 +808,13 @@ def run_reference(args):
 
 
 def _u_ball_problem(macro):
-    """Config-5 macro problem (macro^3 Hex8, fixed 12^3 RVE at every point)."""
+    """The large 3D macro problem of the surrogate comparison (macro^3 Hex8, the fixed 12^3 RVE at every point)."""
     import synth
-    return synth.config5(macro=macro)
+    return synth.cantilever_3d_fixed_rve(macro=macro)
 
 
 def _heldout_oracle():
-    """The stored FP64 oracle values of the config-4 held-out set (tests/golden/c4_heldout_oracle.txt,
+    """The stored FP64 oracle values of the surrogate workload's held-out set (tests/golden/c4_heldout_oracle.txt,
     written by tests/golden/make_c4_heldout.py from oracle/ only): {q: (status, P[9], W)}."""
     path = os.path.join(ROOT, "tests", "golden", "c4_heldout_oracle.txt")
     out = {}
@@ -829,7 +829,7 @@ def _heldout_oracle():
 
 
 def run_c4(args):
-    """Surrogate training workload (config 4): GPU RVE solves at U uniform in |U - I| <= 0.3 on the
+    """Surrogate training workload (c4): GPU RVE solves at U uniform in |U - I| <= 0.3 on the
     fixed 12^3 two-inclusion RVE (training targets), training with the library's BF16 kernels, and
     the held-out stress error: against the GPU RVE solves of the whole held-out set and against the
     stored FP64 oracle values of its first points; by stretch radius, with the largest trust radius
@@ -945,7 +945,7 @@ def run_c4(args):
 
 
 def run_c5(args):
-    """Config 5: one macro iteration of the surrogate-with-fallback path vs the plain GPU RVE path
+    """Surrogate comparison (c5): one macro iteration of the surrogate-with-fallback path vs the plain GPU RVE path
     from the same macro state (macro^3 Hex8, the fixed 12^3 RVE everywhere).  The surrogate
     iteration is timed in the state its own load path left (fallback points solve from whatever
     fluctuations they last committed); the plain iteration is timed after every point's RVE has
@@ -1109,7 +1109,7 @@ def run_hconv(args):
     grid n = 4, 8, ... resolves exactly, solved on the GPU in FP64 at a finite-strain Fbar with
     periodic and with KUBC coupling; relative errors of Pbar and Abar against the finest grid and
     the observed orders.  Also the modelling error of KUBC (Eq. ModelingError): the KUBC-periodic
-    gap of Abar on k x k tilings of one cell, and the macro displacement of the config-1 problem
+    gap of Abar on k x k tilings of one cell, and the macro displacement of the 4x4 Q1 uniaxial problem
     computed with RVE grids 8, 16, 32 of the same microstructure."""
     import dataclasses
 
@@ -1160,8 +1160,8 @@ def run_hconv(args):
     _, Ak = batch(2, [8 * k for k in ks], tiles, 1)
     out["kubc_gap"] = {"tilings": ks, "gap_A": [rel(Ak[j], Ap[j]) for j in range(len(ks))],
                        "periodic_tiling_invariance": [rel(Ap[j], Ap[0]) for j in range(len(ks))]}
-    # the macro problem of config 1 with RVE grids 8, 16, 32 of the box microstructure
-    base = synth.config1()
+    # the 4x4 Q1 uniaxial macro problem with RVE grids 8, 16, 32 of the box microstructure
+    base = synth.uniaxial_2d_small()
     us = {}
     for n in (8, 16, 32):
         p = dataclasses.replace(base, rve_n=np.array([n]), rve_phase=[synth.box_inclusion(n, 2)])
@@ -1186,11 +1186,11 @@ def run_schemes(args):
     import synth
     from paper_1908_08292_gb300.driver import LoadStepDriver
     torch.cuda.set_device(0)
-    cases = [("c1 2D 4x4 Q1 macro, 64 qps, 8x8 RVE (FP64), 10 steps", synth.config1(), 10, {}),
+    cases = [("c1 2D 4x4 Q1 macro, 64 qps, 8x8 RVE (FP64), 10 steps", synth.uniaxial_2d_small(), 10, {}),
              ("c2-shaped 2D 8x8 Q1 macro, 256 qps, 32x32 RVEs (mixed), 5 of 20 steps",
-              synth.config2(macro=8, rve=32), 5, {}),
+              synth.biaxial_shear_2d(macro=8, rve=32), 5, {}),
              ("c3-shaped 3D 4^3 Hex8 macro, 512 qps, 8/12/16^3 RVEs (mixed), 4 of 10 steps",
-              synth.config3(macro=4), 4, {})]
+              synth.uniaxial_3d_uneven(macro=4), 4, {})]
     from paper_1908_08292_gb300 import FehmmError
     out = []
     for name, p, steps, opts in cases:

@@ -138,7 +138,7 @@ def _uniaxial_rollers(macro_n, stretch):
     return dofs[order].astype(np.int64), vals[order]
 
 
-def config1() -> Problem:
+def uniaxial_2d_small() -> Problem:
     """2D plane strain, 4x4 Q1 macro (64 qps), one 8x8 RVE with a centred circle r = 0.25."""
     phase = phase_from_inclusions(8, 2, [[0.5, 0.5]], [0.25])
     dofs, vals = _uniaxial_rollers((4, 4), 0.1)
@@ -147,7 +147,7 @@ def config1() -> Problem:
                    np.zeros(64, dtype=np.int64), dofs, vals, 10, "fp64", 1e-10)
 
 
-def config2(macro: int = 32, rve: int = 32, seed: int = 1002, n_rve: int | None = None,
+def biaxial_shear_2d(macro: int = 32, rve: int = 32, seed: int = 1002, n_rve: int | None = None,
             macro_y: int | None = None) -> Problem:
     """2D batch: macro macro x macro_y (default square) Q1 on the unit square (4 qps/element, one
     RVE each) of rve x rve RVEs, random circle (centre uniform, r ~ U(0.15, 0.35)), stiffness
@@ -177,7 +177,7 @@ def sphere_rve(n: int, n_incl: int, phi: float, centers) -> np.ndarray:
     return phase_from_inclusions(n, 3, centers, np.full(n_incl, r))
 
 
-def config3(macro: int = 8, seed: int = 1003, sizes=(8, 12, 16), n_rve: int | None = None) -> Problem:
+def uniaxial_3d_uneven(macro: int = 8, seed: int = 1003, sizes=(8, 12, 16), n_rve: int | None = None) -> Problem:
     """3D uneven batch: macro macro^3 Hex8 (8 qps/element, one RVE each); RVE n drawn from
     `sizes`, 1-4 spherical inclusions, volume fraction U(0.1, 0.3), stiffness ratio 10."""
     n_qp = macro ** 3 * 8
@@ -200,14 +200,14 @@ def config3(macro: int = 8, seed: int = 1003, sizes=(8, 12, 16), n_rve: int | No
 
 
 def fixed_rve12(seed: int = 1004, n: int = 12) -> tuple:
-    """The fixed two-inclusion microstructure (config-3 generator, n_incl = 2) on an n^3 grid
+    """The fixed two-inclusion microstructure (the 3D workload generator, n_incl = 2) on an n^3 grid
     (12^3 in the workloads; smaller grids of the same geometry serve quick tests)."""
     u = uniform(seed, np.array([0]), 7)[0]
     phi = 0.1 + 0.2 * u[0]
     return sphere_rve(n, 2, phi, u[1:7].reshape(2, 3)), phi
 
 
-def config5(macro: int = 16) -> Problem:
+def cantilever_3d_fixed_rve(macro: int = 16) -> Problem:
     """3D large macro: macro^3 Hex8 (8 qps/element), all with the fixed 12^3 RVE; clamped at
     x = 0, u = (F - I) X at x = 1 with F_end - I = 0.35 (e1 x e1 + e1 x e2)/sqrt(2)."""
     phase, phi = fixed_rve12()

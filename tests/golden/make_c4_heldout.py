@@ -1,6 +1,6 @@
 """Write c4_heldout_oracle.txt: the FP64 oracle's homogenised stress Pbar and energy Wbar of the
-fixed 12^3 two-inclusion RVE (the config-4 microstructure of synth.fixed_rve12, matrix E = 1,
-inclusions E = 10, nu = 0.3) at the first N held-out right stretches U of the config-4 sampler
+fixed 12^3 two-inclusion RVE (the surrogate workload's microstructure, synth.fixed_rve12, matrix E = 1,
+inclusions E = 10, nu = 0.3) at the first N held-out right stretches U of that workload's sampler
 (synth.stretch_ball, seed 2004, |U - I|_F <= 0.3).
 
 Calls only oracle/ and synth/ (test infrastructure).  Each point is solved from zero fluctuation

@@ -43,7 +43,7 @@ def _free_port():
 
 
 def _problem():
-    return synth.config2(macro=2, rve=8, seed=1002)
+    return synth.biaxial_shear_2d(macro=2, rve=8, seed=1002)
 
 
 def _iteration_inputs():

@@ -30,9 +30,9 @@ def test_autotune_then_oracle_parity_and_cache(dim, tmp_path):
 
     import paper_1908_08292_gb300 as fe
     if dim == 2:
-        p = synth.config2(macro=4, rve=32)  # 64 points of 32x32 RVEs
+        p = synth.biaxial_shear_2d(macro=4, rve=32)  # 64 points of 32x32 RVEs
     else:
-        p = synth.config3(macro=1, sizes=(8, 12), n_rve=8)  # 8 points, uneven 8^3 / 12^3
+        p = synth.uniaxial_3d_uneven(macro=1, sizes=(8, 12), n_rve=8)  # 8 points, uneven 8^3 / 12^3
     d, n_qp = p.dim, p.n_qp
     Fs = synth.random_F(801 + dim, n_qp, d, 0.08)
     F = torch.tensor(Fs.reshape(n_qp, d * d), dtype=torch.float64, device="cuda")

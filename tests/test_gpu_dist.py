@@ -15,7 +15,7 @@ def test_two_shards_sum_to_the_full_iteration():
     import paper_1908_08292_gb300 as fe
     from paper_1908_08292_gb300.dist import Shard, ShardedIteration
     dev = torch.device("cuda:0")
-    p = synth.config2(macro=4, rve=8, macro_y=8)  # 128 qps, one RVE each
+    p = synth.biaxial_shear_2d(macro=4, rve=8, macro_y=8)  # 128 qps, one RVE each
     n_qp, d = p.n_qp, 2
     u = torch.zeros(2 * 5 * 9, dtype=torch.float64, device=dev)
     u[torch.tensor(p.dirichlet_dofs, device=dev)] = torch.tensor(p.dirichlet_end / p.n_steps, device=dev)

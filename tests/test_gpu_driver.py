@@ -91,12 +91,12 @@ def test_macro_solve_repeatable_with_one_block_per_sm():
 
 
 @pytest.mark.parametrize("scheme", ["nested", "alternating"])
-def test_config1_load_steps_match_oracle(scheme):
-    """All ten load steps of config 1 (uniaxial stretch to 10 %) against the oracle's Algorithm 1
+def test_uniaxial_2d_load_steps_match_oracle(scheme):
+    """All ten load steps of the 4x4 Q1 uniaxial problem (stretch to 10 %) against the oracle's Algorithm 1
     or 2."""
     from paper_1908_08292_gb300.driver import LoadStepDriver
 
-    p = synth.config1()
+    p = synth.uniaxial_2d_small()
     steps = 10
     ref, mesh = odriver.run(p, scheme=scheme, steps_to_run=steps, micro_rtol=1e-12)
     drv = LoadStepDriver(p, precision="fp64", scheme=scheme, newton_rtol=1e-12, newton_atol=1e-15, cg_rtol=1e-9,
@@ -115,13 +115,13 @@ def test_config1_load_steps_match_oracle(scheme):
         drv.close()
 
 
-def test_config1_tangent_predictor_matches_oracle():
+def test_uniaxial_2d_tangent_predictor_matches_oracle():
     """Load steps that start from the tangent predictor (the Dirichlet increment's load on the
     last converged tangent and the interior correction it implies) against the oracle's driver
     with the same predictor: same macro iterations, same displacements and stresses."""
     from paper_1908_08292_gb300.driver import LoadStepDriver
 
-    p = synth.config1()
+    p = synth.uniaxial_2d_small()
     steps = 4
     ref, mesh = odriver.run(p, scheme="nested", steps_to_run=steps, micro_rtol=1e-12, predictor=True)
     drv = LoadStepDriver(p, precision="fp64", scheme="nested", newton_rtol=1e-12, newton_atol=1e-15, cg_rtol=1e-9,
@@ -143,7 +143,7 @@ def test_config1_tangent_predictor_matches_oracle():
 def test_graph_replay_equals_eager():
     from paper_1908_08292_gb300.driver import LoadStepDriver
 
-    p = synth.config1()
+    p = synth.uniaxial_2d_small()
     out = []
     for graphs in (False, True):
         drv = LoadStepDriver(p, precision="mixed", graphs=graphs)

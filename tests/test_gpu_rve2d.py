@@ -30,7 +30,7 @@ def check(out, refs, tol, check_W=False):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_config1_rve_random_F(precision):
+def test_small_rve_random_F(precision):
     n = 8
     phase = synth.phase_from_inclusions(n, 2, [[0.5, 0.5]], [0.25])
     Fs = synth.random_F(101, 12, 2, 0.15)
@@ -67,10 +67,10 @@ def test_uneven_sizes_one_launch(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_config2_sized_rves(precision):
-    """32x32 RVEs drawn from the config-2 generator (the benchmark's workload) at
+def test_workload_2d_sized_rves(precision):
+    """32x32 RVEs drawn from the 2D workload generator (the benchmark's RVEs) at
     deformation gradients along its load path (biaxial 30% + shear 0.3)."""
-    p = synth.config2(macro=1, rve=32, n_rve=4)
+    p = synth.biaxial_shear_2d(macro=1, rve=32, n_rve=4)
     F_end = p.extra["F_end"]
     lams = [0.05, 0.3, 0.7, 1.0]
     Fs = np.array([np.eye(2) + l * (F_end - np.eye(2)) for l in lams])

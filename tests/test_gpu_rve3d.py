@@ -46,9 +46,9 @@ def test_uneven_small_sizes_one_launch(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_config3_generator_rves(precision):
-    """8^3 RVEs of the config-3 generator (1-4 spheres, ratio 10) along its uniaxial load path."""
-    p = synth.config3(macro=1, sizes=(8,), n_rve=3)
+def test_workload_3d_generator_rves(precision):
+    """8^3 RVEs of the 3D workload generator (1-4 spheres, ratio 10) along its uniaxial load path."""
+    p = synth.uniaxial_3d_uneven(macro=1, sizes=(8,), n_rve=3)
     Fs = np.array([np.diag([1.0 + s, 1.0 - 0.3 * s, 1.0 - 0.3 * s]) for s in (0.02, 0.1, 0.2)])
     opts = STRICT if precision == "fp64" else {}
     out = gpu_batch(3, precision, p.rve_n, p.rve_phase, p.rve_E, p.rve_nu, np.arange(3), Fs, flags=4, **opts)
@@ -63,11 +63,11 @@ _REF16 = {}
 
 
 def _ref16():
-    """One 16^3 RVE of the config-3 generator (the largest grid of that workload: 12288 dofs,
+    """One 16^3 RVE of the 3D workload generator (the largest grid of that workload: 12288 dofs,
     three coarse levels 8, 4, 2) at a tension-shear Fbar, solved once by the oracle (about 100 s
     of sparse LU) and shared by the two precisions."""
     if not _REF16:
-        p = synth.config3(macro=1, sizes=(16,), n_rve=1)
+        p = synth.uniaxial_3d_uneven(macro=1, sizes=(16,), n_rve=1)
         F = np.eye(3) + np.array([[0.08, 0.04, 0.0], [0.02, -0.02, 0.03], [0.0, 0.01, -0.02]])
         ref = PeriodicRVE(16, 3, p.rve_phase[0], p.rve_E[0], p.rve_nu[0]).solve(F, rtol=1e-13, atol=1e-16)
         _REF16.update(p=p, F=F, ref=ref)
@@ -75,13 +75,13 @@ def _ref16():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_config3_16cubed_rve(precision):
-    """The 16^3 Hex8 RVE of the config-3 workload (largest scratch and multigrid depth) against
+def test_workload_3d_16cubed_rve(precision):
+    """The 16^3 Hex8 RVE of the 3D workload (largest scratch and multigrid depth) against
     the oracle: P and A per point at 1e-10 (FP64) / 1e-5 (mixed), with the 8^3 and 12^3 grids of
     the same workload in the same launch."""
     r16 = _ref16()
     p = r16["p"]
-    small = synth.config3(macro=1, sizes=(8, 12), n_rve=2, seed=1013)
+    small = synth.uniaxial_3d_uneven(macro=1, sizes=(8, 12), n_rve=2, seed=1013)
     sizes = [16] + [int(n) for n in small.rve_n]
     phases = [p.rve_phase[0]] + list(small.rve_phase)
     E = [p.rve_E[0]] + list(small.rve_E)

@@ -51,9 +51,9 @@ def test_patch_test_affine_field(n):
 
 
 def test_nested_run_homogeneous_config1_closed_form():
-    """Config-1 boundary conditions with a homogeneous microstructure: the macro solution is the
+    """The 4x4 Q1 uniaxial boundary conditions with a homogeneous microstructure: the macro solution is the
     uniaxial plane-strain state F = diag(s, t), t^2 = (lam/2 + mu)/(lam s^2/2 + mu)."""
-    p = synth.config1()
+    p = synth.uniaxial_2d_small()
     p.rve_E[:] = 1.0
     recs, mesh = driver.run(p, n_steps=10, steps_to_run=3)
     lam, mu = mat.lame(1.0, 0.3)
@@ -68,7 +68,7 @@ def test_nested_run_homogeneous_config1_closed_form():
 
 def test_nested_and_alternating_reach_same_state():
     """Both schemes satisfy the same discrete equations at the end of a load step (Sec. 5)."""
-    p = synth.config1()
+    p = synth.uniaxial_2d_small()
     nested, _ = driver.run(p, scheme="nested", steps_to_run=2)
     alt, _ = driver.run(p, scheme="alternating", steps_to_run=2)
     for a, b in zip(nested, alt):

@@ -70,7 +70,7 @@ def test_homogeneous_rve_is_closed_form(d):
     np.testing.assert_allclose(out["W"], mat.psi(Fbar, lam, mu), atol=1e-14)
 
 
-def test_config1_uniaxial_closed_form_on_homogeneous_rve():
+def test_uniaxial_closed_form_on_homogeneous_rve():
     lam, mu = mat.lame(1.0, 0.3)
     s = 1.1
     t = np.sqrt((lam / 2 + mu) / (lam * s * s / 2 + mu))
