@@ -1263,7 +1263,7 @@ def main():
     ap.add_argument("--c4-samples", type=int, default=204800)
     ap.add_argument("--c4-holdout", type=int, default=10240)
     ap.add_argument("--c4-epochs", type=int, default=2400)
-    ap.add_argument("--c4-lr", type=float, default=2e-3, help="peak AdamW learning rate (cosine decay to 1/100)")
+    ap.add_argument("--c4-lr", type=float, default=1e-3, help="peak AdamW learning rate (cosine decay to 1/100)")
     ap.add_argument("--c4-out-scale", type=float, default=0.0,
                     help="scale of the network's initial output weights (0: zero output layer)")
     ap.add_argument("--c4-hessian-origin", type=int, default=1,
