@@ -76,3 +76,19 @@ def test_surrogate_base_law_projection(L):
     # the projection removes the isotropic content: the remainder has no bulk or shear trace
     R = A - iso
     assert abs(np.einsum("iijj->", R)) < 1e-12 and abs(np.einsum("ijij->", R)) < 1e-12
+
+
+def test_surrogate_polynomial_and_mlp_argument_errors(L):
+    """Invalid arguments of the polynomial fit and the MLP status check are rejected on the host,
+    before any device call; the parameter struct carries the 896 polynomial coefficients."""
+    from paper_1908_08292_gb300.surrogate import POLY_TERMS, SurrogateParams
+    sp = SurrogateParams()
+    assert POLY_TERMS == 896 and len(sp.poly) == 896
+    assert ctypes.sizeof(SurrogateParams) == 8 * (5 + 36 + 1 + 6 + 36 + 896)
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the checks come first
+    for deg in (2, 7):
+        assert L.fehmm_surrogate_fit_poly(ctypes.byref(sp), dummy, dummy, dummy, 10, deg, None) == -1
+    assert L.fehmm_surrogate_fit_poly(None, dummy, dummy, dummy, 10, 6, None) == -1
+    assert L.fehmm_surrogate_fit_poly(ctypes.byref(sp), dummy, dummy, dummy, 0, 6, None) == -1
+    flag = ctypes.c_int(0)
+    assert L.fehmm_mlp_check(None, ctypes.byref(flag)) == -1
