@@ -1595,41 +1595,62 @@ __device__ void solve_item_2d(const Rve2dArgs& a, int qp, const Smem2D<TA>& sm, 
   const bool want_A = usable && !(a.flags & kFlagNoTangent) && a.A != nullptr;
   if (want_A) {
     const TA Fb[4] = {(TA)sm.misc[0], (TA)sm.misc[1], (TA)sm.misc[2], (TA)sm.misc[3]};
-    build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb, mg);
     vec2_t<TA>* X = Xs;
     // kept solutions of this point's previous transfer solves ([4][NN] vec2, zero at first)
     const bool warm = a.X_in != nullptr;
     const vec2_t<TA>* X0 = warm ? reinterpret_cast<const vec2_t<TA>*>(a.X_in) + 2 * w_off : nullptr;
     const TA omega0 = mg.omega;
-    for (int c = 0; c < 4; ++c) {
-      TA b[4] = {TA(0), TA(0), TA(0), TA(0)};
-      if (o.active) {
-        const vec2_t<TA> b0 = Lb[c * NN + o.node[0]], b1 = Lb[c * NN + o.node[1]];
-        b[0] = b0.x;
-        b[1] = b0.y;
-        b[2] = b1.x;
-        b[3] = b1.y;
-      }
-      int pst = kStatusOk, ci = 0;
-      for (;;) {  // as for the Newton corrections: a breakdown is retried with half the damping
-        if (warm && o.active) {
-#pragma unroll
-          for (int s = 0; s < 2; ++s)
-            X[c * NN + o.node[s]] = o.pin[s] ? mk2<TA>(TA(0), TA(0)) : X0[c * NN + o.node[s]];
+    // The coarse levels the final Newton stage built (at its first iteration, when it iterated at
+    // all) are kept for the transfer too, as for the later Newton iterations: its fine level is
+    // the converged tangent.  A transfer PCG that breaks down or hits its cap with kept levels
+    // rebuilds the whole tangent with fresh levels and starts the transfer again.
+    bool reuse_t = kMG && mg.levels && a.mg_reuse && it > 0;
+    for (;;) {
+      build_tangent<TA, REG, kMG, LAW>(o, sm, stage_k, Fb, phase, S, Minv, true, Lb, mg, !reuse_t);
+      bool redo = false;
+      int t_total = 0, t_max = 0, t_status = kStatusOk;
+      for (int c = 0; c < 4; ++c) {
+        TA b[4] = {TA(0), TA(0), TA(0), TA(0)};
+        if (o.active) {
+          const vec2_t<TA> b0 = Lb[c * NN + o.node[0]], b1 = Lb[c * NN + o.node[1]];
+          b[0] = b0.x;
+          b[1] = b0.y;
+          b[2] = b1.x;
+          b[3] = b1.y;
         }
-        ci += pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, X + c * NN, (TA)a.cond_rtol, a.max_cond_cg, sm.p, redD, &pst,
-                                     false, warm);
-        __syncthreads();
-        if (!(kMG && mg.levels && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap) &&
-              mg.omega > TA(0.2) * omega0))
-          break;
-        mg.omega *= TA(0.5);
-        pst = kStatusOk;
+        int pst = kStatusOk, ci = 0;
+        for (;;) {  // as for the Newton corrections: a breakdown is retried with half the damping
+          if (warm && o.active) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+              X[c * NN + o.node[s]] = o.pin[s] ? mk2<TA>(TA(0), TA(0)) : X0[c * NN + o.node[s]];
+          }
+          ci += pcg_pair<TA, REG, kMG>(S, o, Minv, mg, b, X + c * NN, (TA)a.cond_rtol, a.max_cond_cg, sm.p, redD,
+                                       &pst, false, warm);
+          __syncthreads();
+          if (reuse_t && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap)) {
+            redo = true;
+            break;
+          }
+          if (!(kMG && mg.levels && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap) &&
+                mg.omega > TA(0.2) * omega0))
+            break;
+          mg.omega *= TA(0.5);
+          pst = kStatusOk;
+        }
+        mg.omega = omega0;
+        t_total += ci;
+        t_max = ci > t_max ? ci : t_max;
+        if (redo) break;
+        if (pst != kStatusOk && t_status == kStatusOk) t_status = pst;
       }
-      mg.omega = omega0;
-      cond_total += ci;
-      cond_max = ci > cond_max ? ci : cond_max;
-      if (pst != kStatusOk && status == kStatusOk) status = pst;
+      cond_total += t_total;
+      cond_max = t_max > cond_max ? t_max : cond_max;
+      if (!redo) {
+        if (t_status != kStatusOk && status == kStatusOk) status = t_status;
+        break;
+      }
+      reuse_t = false;
     }
     __syncthreads();
     const vec2_t<TA>* wsrc;
