@@ -1419,8 +1419,8 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
       // stretch and stiffness contrast.  So a PCG that breaks down, hits its cap or sees negative
       // curvature (which an indefinite V-cycle can fake) with reused levels is run again once
       // with levels rebuilt at the current tangent (its right-hand side
-      // is kept in the transfer area, unused during Newton).  The tangent transfer always
-      // rebuilds them at the converged state.
+      // is kept in the transfer area, unused during Newton).  The tangent transfer keeps them
+      // too (rebuilding them only after a breakdown or cap).
       // A V-cycle whose fresh levels still break down (its damped smoother no longer contracts at
       // this tangent) is retried with half the damping, down to omega / 8.
       bool reused = c.mg.levels && it > 0 && a.mg_reuse;
@@ -1494,7 +1494,11 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
 #pragma unroll
     for (int k = 0; k < 45; ++k) As[k] = 0.0;
     tangent3<TA, LAW, true>(c, w, As);
-    if (c.mg.levels) mg3_build<TA, LAW>(c);
+    // the coarse levels of this solve's last tangent (when its Newton loop iterated at all) are
+    // kept for the transfer as for the later Newton iterations; a transfer PCG that breaks down or
+    // hits its cap with them is run again with levels rebuilt at the converged state
+    bool reuse_t = c.mg.levels && a.mg_reuse && it > 0;
+    if (c.mg.levels && !reuse_t) mg3_build<TA, LAW>(c);
     // <A>: 45 FP64 sums in three reductions of 15
     for (int part = 0; part < 3; ++part) block_sum_n<double>(As + 15 * part, 15, c.red);
     // right-hand sides L_c (c = 3k + L) stored [c][3][NN]
@@ -1520,6 +1524,12 @@ __device__ void solve_item_3d(const Rve2dArgs& a, int qp, unsigned char* smem, u
         }
         __syncthreads();
         ci += pcg3<TA, LAW>(c, (TA)a.cond_rtol, a.max_cond_cg, false, &pst, warm);
+        if (reuse_t && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap)) {
+          mg3_build<TA, LAW>(c);
+          reuse_t = false;
+          pst = kStatusOk;
+          continue;
+        }
         if (!(c.mg.levels && (pst == kStatusPcgBreakdown || pst == kStatusPcgCap) && c.mg.omega > TA(0.2) * omega0))
           break;
         c.mg.omega *= TA(0.5);
