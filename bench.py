@@ -73,13 +73,10 @@ FP64_PEAK_TFLOPS = 1.25                              # GB300 nominal FP64
 
 # DRAM bytes per RVE solve of the dominant kernel from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch / RVEs in that launch), with the profile summary it comes
-# from; scaled to a launch of the bench by the RVEs it solves.  Captured on smaller launches of
-# the same kernel build (1024 RVEs of c2, 64 of c3); the bytes per RVE are the state each solve
-# reads and writes plus scratch write-back, which grow with the RVEs of a launch.
-TRAFFIC_PER_LAUNCH = {
-    ("c2", "mg"): ((53123072 + 105645568) / 1024, "profiles/rve2d_kernel_mg_c2_macro16.md"),
-    ("c3", "mg"): ((1031852000 + 500233472) / 64, "profiles/rve3d_kernel_mg_c3_macro2.md"),
-}
+# from; scaled to a launch of the bench by the RVEs it solves.  Only for a capture of the kernel
+# build the bench runs: the captures in profiles/ (155 KB per 2D RVE, 23.9 MB per 3D RVE) predate
+# the kernels' keeping of the coarse levels for the tangent transfer, so no entry is given.
+TRAFFIC_PER_LAUNCH = {}
 
 
 def workload_config(step_index):
